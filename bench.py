@@ -1,0 +1,414 @@
+"""Benchmark: SSP-RK3 time steps of the modal DG Euler residual on one GB300.
+
+One step = one SSP-RK3 step = 3 fused residual + stage-update launches over
+the whole mesh (every row of the hot path: interpolation, fluxes, Riemann
+solver, lift, inverse mass, RK axpy).  Metric: residual DOF-updates per
+second = 3 * N_e * 5 * N_b / t_step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3]
+                    [--precision auto|fp64|fp32] [--impl ours|reference]
+
+Workloads (seeded, synthetic; they stand in for the paper's 2D grids):
+  c1  6^3 x 6 periodic cube, P1, jitter 10%   (1,296 tets)
+  c2  48^3 x 6 periodic cube, P2, jitter 10%  (663,552 tets), vortex + 1% noise
+  c3  64^3 x 6 periodic cube, P3, jitter 15%  (1,572,864 tets), vortex, Roe
+  c4  32^3 x 6 periodic cube, P2              (196,608 tets)
+  c5  96x48x48 x 6 box channel, P3, walls + far field (1,327,104 tets), pulse
+The default is c3 (the P3 workload the HBM-roofline target refers to).
+
+Multi-GPU (torchrun): every rank runs its own copy of the workload on its
+own GPU (replicas; the residual needs no exchange for independent meshes);
+value = all ranks' DOF-updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "c1": dict(n=6, p=1, jitter=0.10, flux="rusanov", field="vortex", box=False),
+    "c2": dict(n=48, p=2, jitter=0.10, flux="rusanov", field="vortex_noise", box=False),
+    "c3": dict(n=64, p=3, jitter=0.15, flux="roe", field="vortex", box=False),
+    "c4": dict(n=32, p=2, jitter=0.10, flux="rusanov", field="vortex", box=False),
+    "c5": dict(dims=(96, 48, 48), p=3, jitter=0.15, flux="roe", field="pulse", box=True),
+    # small case of the c3 kernel for profiler captures (state 157 MB > L2)
+    "c3s": dict(n=32, p=3, jitter=0.15, flux="roe", field="vortex", box=False),
+}
+NB = {1: 4, 2: 10, 3: 20}
+NQ = {1: 4, 2: 14, 3: 24}
+NQF = {1: 3, 2: 6, 3: 12}
+# FP64 flops of one Riemann solve per face point (counted from the formulas, divisions and
+# square roots as one flop each)
+RIEMANN_FLOPS = {"rusanov": 70, "roe": 160}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def make_workload(name):
+    from paper_2209_01877_gb300 import inputs as I
+    w = WORKLOADS[name]
+    if w["box"]:
+        mesh = I.make_box_channel(*w["dims"], jitter=w["jitter"])
+    else:
+        mesh = I.make_periodic_cube(w["n"], jitter=w["jitter"])
+    if w["field"] == "pulse":
+        c = I.pulse_centre()
+        field = lambda x: I.gaussian_pulse(x, c)
+    else:
+        field = lambda x: I.isentropic_vortex(x)
+    return mesh, field, w
+
+
+def algorithmic_model(p, ne, flux, s_state, stage):
+    """Bytes and flops of one fused residual + RK-stage launch (the minimum the
+    method needs): the state read once, the RK base state read (stages 2, 3),
+    the new state written, 32 B of connectivity/geometry per element; flops
+    with every interior face's traces and Riemann solve counted once."""
+    nb, nq, nqf = NB[p], NQ[p], NQF[p]
+    nv = 5 * nb
+    reads = 2 if stage > 1 else 1
+    bytes_ = ne * (nv * s_state * (reads + 1) + 32)
+    per_elem = (2 * 2 * nqf * 5 * nb * 2          # traces: 2 faces/elem x 2 sides
+                + 2 * nqf * RIEMANN_FLOPS[flux]   # Riemann: 2 faces/elem
+                + nq * 5 * nb * 2                 # volume interpolation
+                + nq * (25 + 45 * 2)              # Euler flux + contravariant transform
+                + 5 * nb * 3 * nq * 2             # projection on the basis gradients
+                + 5 * nb * 4 * nqf * 2            # lift of the 4 face fluxes
+                + nv * 4)                         # RK stage
+    return bytes_, ne * per_elem
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+def fp64_peak_tflops(sm_mhz=2070.0):
+    """FP64 FMA peak of GB300: 152 SMs x 2 FP64 FMA/clk/SM (4 flop/clk/SM) x clock."""
+    return 152 * 4 * sm_mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, device):
+    import torch
+    from paper_2209_01877_gb300 import dg
+
+    mesh, field, w = make_workload(args.workload)
+    p, flux = w["p"], w["flux"]
+    precision = {"auto": dg.DG_FP64, "fp64": dg.DG_FP64, "fp32": dg.DG_FP32}[args.precision]
+    fs = (0, 0, 0, 0, 0)
+    if w["box"]:
+        from paper_2209_01877_gb300 import inputs as I
+        fs = tuple(I.freestream_state(0.3))
+    t0 = time.time()
+    M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, None if not w["box"] else mesh.bc_tag, order=p, precision=precision,
+                flux=dg.DG_ROE if flux == "roe" else dg.DG_RUSANOV, renumber=dg.DG_ORDER_RCM, freestream=fs)
+    U0 = M.project(field)
+    if w["field"] == "vortex_noise":
+        from paper_2209_01877_gb300 import inputs as I
+        U0 = I.perturb_coefficients(U0)
+    log(f"[rank {rank}] mesh + state ready in {time.time() - t0:.1f}s: ne={mesh.ne} p={p} {flux}")
+    stream = torch.cuda.current_stream(device)
+    dg.dg_set_state(M.handle, U0, stream)
+    dt = dg.dg_stable_dt(M.handle, 0.1, stream)
+    ne, nb = mesh.ne, NB[p]
+    dofs = ne * 5 * nb
+
+    for _ in range(args.warmup):
+        dg.dg_rk3_step(M.handle, dt, 1, stream)
+    torch.cuda.synchronize(device)
+    dg.dg_sync_status(M.handle, stream)
+
+    # timed region: K steps, events around every stage launch
+    nev = 3 * args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nev)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(device.index if device.index is not None else 0)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(device)
+    clocks.start()
+    time.sleep(0.3)
+    start.record(stream)
+    k = 0
+    for _ in range(args.steps):
+        for st in (1, 2, 3):
+            ev[k][0].record(stream)
+            dg.dg_rk_stage(M.handle, st, dt, stream)
+            ev[k][1].record(stream)
+            k += 1
+    stop.record(stream)
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    dg.dg_sync_status(M.handle, stream)
+    t_total = start.elapsed_time(stop) / 1e3
+    stage_ms = [[], [], []]
+    for i, (a, b) in enumerate(ev):
+        stage_ms[i % 3].append(a.elapsed_time(b))
+    t_local = t_total
+    if world > 1:
+        t = torch.tensor([t_total], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(t.item())
+    ms_per_step = t_total / args.steps * 1e3
+    value = world * 3 * dofs * args.steps / t_total
+
+    # roofline of the dominant kernel (the fused residual + RK-stage kernel)
+    s_state = 8 if precision == dg.DG_FP64 else 4
+    peaks, peak_src = measured_peaks()
+    tot_bytes = tot_flops = tot_ms = 0.0
+    for st in (1, 2, 3):
+        b, f = algorithmic_model(p, ne, flux, s_state, st)
+        tot_bytes += b * len(stage_ms[st - 1])
+        tot_flops += f * len(stage_ms[st - 1])
+        tot_ms += sum(stage_ms[st - 1])
+    nlaunch = sum(len(x) for x in stage_ms)
+    avg_ms = tot_ms / nlaunch
+    bytes_per_launch = tot_bytes / nlaunch
+    flops_per_launch = tot_flops / nlaunch
+    hbm_achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    if precision == dg.DG_FP64:
+        peak_alu = fp64_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+                "frac": achieved / peak_alu, "traffic": None,
+                "peak_source": "FP64 FMA pipe: 152 SMs x 4 flop/clk x max SM clock (recipe unit counts and clock)",
+                "hbm_achieved_gbs": hbm_achieved, "hbm_frac": hbm_achieved / peaks["hbm_gbs"],
+                "kernel": "k_residual<double,P,FLUX,RK>", "algorithmic_bytes_per_launch": bytes_per_launch,
+                "algorithmic_flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm_achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": f"hbm_gbs of {peak_src} peaks", "kernel": "k_residual<float,P,FLUX,RK>",
+                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Uh = torch.empty((ne, 5, nb), dtype=torch.float64, pin_memory=True).numpy()
+        Uh[...] = U0
+        nrep = max(1, min(args.steps, 5))
+        dg.dg_rk3_step(M.handle, dt, 1, stream)
+        torch.cuda.synchronize(device)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(nrep):
+            dg.dg_set_state(M.handle, Uh, stream)
+            dg.dg_rk3_step(M.handle, dt, 1, stream)
+            dg.dg_get_state(M.handle, Uh, stream)
+        b.record(stream)
+        torch.cuda.synchronize(device)
+        te = a.elapsed_time(b) / 1e3
+        e2e = {"value": world * 3 * dofs * nrep / te, "unit": "DOF-updates/s", "h2d_bytes_per_step": dofs * 8,
+               "d2h_bytes_per_step": dofs * 8, "steps": nrep}
+    M.close()
+    return dict(value=value, ms_per_step=ms_per_step, roofline=roof, clocks=clk, e2e=e2e, t_local=t_local,
+                precision="f64" if precision == dg.DG_FP64 else "f32", ne=ne, p=p, flux=flux,
+                stage_ms=[float(np.mean(x)) for x in stage_ms], nlaunch=nlaunch)
+
+
+# ---------------------------------------------------------------------------------------------
+def oracle_sample_rate(workload, nsample, reps=1, seed=11):
+    """The FP64 oracle's residual on a seeded sample of the workload's
+    elements, single-threaded: (DOF-updates/s, seconds, sample size)."""
+    from oracle.dg import Problem
+    mesh, field, w = make_workload(workload)
+    fs = None
+    if w["box"]:
+        from paper_2209_01877_gb300 import inputs as I
+        fs = I.freestream_state(0.3)
+    P = Problem(mesh.tet_vid, mesh.tet_xyz, mesh.bc_tag if w["box"] else None, p=w["p"], flux=w["flux"],
+                freestream=fs)
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(mesh.ne, size=min(nsample, mesh.ne), replace=False))
+    need = np.unique(np.concatenate([rows, P.nbr[rows].ravel()]))
+    need = need[need >= 0]
+    U = np.zeros((mesh.ne, 5, P.nb))
+    sub = P.project(field, rule="volume", elems=need)
+    U[need] = sub
+    P.residual(U, rows[:16])
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        P.residual(U, rows)
+    dt = (time.perf_counter() - t0) / reps
+    return len(rows) * 5 * P.nb / dt, dt, len(rows)
+
+
+def cpu_baseline_subprocess(workload, nsample, reps=1):
+    """Run the oracle timing in a child process pinned to one BLAS/OpenMP thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "r = bench.oracle_sample_rate(%r, %d, %d); print(json.dumps(r))" % (ROOT, workload, nsample, reps))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    rate, sec, n = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle residual on {n} seeded elements of {workload} (with their neighbours' "
+                      f"states), {reps} evaluation(s), {sec:.1f}s each, 1 thread"}
+
+
+SAMPLE = {"c1": 1296, "c2": 60000, "c3": 30000, "c4": 60000, "c5": 30000, "c3s": 30000}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, each step a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = config_of(args)
+    n = max(200, SAMPLE.get(args.workload, 2000) // 3)
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline_subprocess(args.workload, n) if i == 0 else None
+        if r is None:
+            rate, _, _ = oracle_sample_rate(args.workload, n, 1, seed=11 + i)
+        else:
+            rate = r["value"]
+        if i >= args.warmup:
+            rates.append(rate)
+    value = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"FP64 oracle residual on {n} seeded elements of {args.workload} per step"},
+            "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+METRIC = "DG residual DOF-updates/s (P1-P3 tets), mixed vs FP64; % of HBM roofline"
+
+
+def config_of(args):
+    w = WORKLOADS[args.workload]
+    from paper_2209_01877_gb300 import inputs as I
+    ne = 6 * (w["n"] ** 3 if not w["box"] else int(np.prod(w["dims"])))
+    desc = {"c1": "6^3x6 periodic cube", "c2": "48^3x6 periodic cube", "c3": "64^3x6 periodic cube",
+            "c4": "32^3x6 periodic cube", "c5": "96x48x48x6 box channel", "c3s": "32^3x6 periodic cube"}
+    return {"workload": f"{args.workload}: {desc[args.workload]}, P{w['p']}, {ne} tets, {w['flux']} flux, "
+                        f"jitter {w['jitter']}, RCM order, field {w['field']}",
+            "tets": ne, "order": w["p"], "flux": w["flux"], "dofs": ne * 5 * I.n_basis(w["p"]),
+            "step": "one SSP-RK3 step = 3 fused residual+stage launches",
+            "l2": "inputs larger than L2 (state >= 157 MB vs 129 MB L2)" if w["p"] >= 2 and ne > 100000
+            else "state fits in L2 (small case)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        log("warmup raised to 3 (timing rule)")
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu_base = cpu_baseline_subprocess(args.workload, SAMPLE.get(args.workload, 20000), reps=2)
+        except Exception as e:  # reported, not fatal
+            cpu_base = {"value": None, "error": str(e)[-300:]}
+    r = run_ours(args, rank, world, device)
+    if rank == 0:
+        line = {"metric": METRIC, "value": r["value"], "unit": "DOF-updates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": r["precision"],
+                "data": "synthetic", "config": config_of(args), "roofline": r["roofline"],
+                "cpu_baseline": cpu_base, "e2e": r["e2e"], "clocks": r["clocks"],
+                "gpu_launches": r["nlaunch"], "stage_ms": r["stage_ms"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * dg.h -- C ABI of a GB300 (sm_103a) modal discontinuous Galerkin solver for
+ * the 3D compressible Euler equations on affine tetrahedra.
+ *
+ * What it computes (arXiv:2209.01877):
+ *   - conservative Euler equations, Sec. II-A, Eq. 1-4 (written in 3D,
+ *     inviscid: the ivis = 0 case of Eq. 1);
+ *   - modal expansion of every conserved variable, Eq. 10, in the orthonormal
+ *     Proriol-Koornwinder-Dubiner basis of the unit tetrahedron;
+ *   - the weak form of Eq. 11 without its viscous lines: volume integral of
+ *     F(Q).grad(b_j), interior-face integral of the numerical flux
+ *     H_c(Q-, Q+, n) b_j (Roe, as in Sec. II-B, or Rusanov), boundary-face
+ *     integral with ghost states, all by Gaussian quadrature exact to degree 2p;
+ *   - the inverse mass matrix (diagonal: |det J| for the orthonormal basis);
+ *   - explicit Runge-Kutta time marching (Sec. III; here SSP-RK3) and the
+ *     global minimum of the local time step (Sec. III-C);
+ *   - grid renumbering by reverse Cuthill-McKee (Sec. III-B).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a dg_status; DG_OK is 0.  On failure
+ *     dg_last_error() returns a message for the calling thread.  The library
+ *     never aborts the process and never traps on the device.
+ *   - Coefficient arrays at this boundary are FP64, [ne][5][Nb] row-major, in
+ *     the caller's element order, variables (rho, rho u, rho v, rho w, E),
+ *     Nb = (p+1)(p+2)(p+3)/6 modes ordered by total degree, then i, then j.
+ *   - Pointers are borrowed for the duration of the call only.  A device
+ *     pointer must live on the mesh's device.  `stream` is a cudaStream_t
+ *     (NULL = legacy default stream); all device work is ordered on it and,
+ *     unless stated otherwise, a call returns before that work completes.
+ *   - Device-side failures (non-positive density or pressure, non-finite
+ *     values) set a status word on the device; dg_sync_status() reads it.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DG_OK = 0,
+    DG_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, bad enum) */
+    DG_ERR_MESH = 2,         /* invalid mesh: non-positive volume, face shared by >2 tets, untagged boundary */
+    DG_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    DG_ERR_OOM = 4,          /* device allocation failed */
+    DG_ERR_NONPHYSICAL = 5,  /* the device saw rho <= 0, p <= 0 or a non-finite value */
+    DG_ERR_NOSTATE = 6,      /* the call needs a state set by dg_set_state */
+    DG_ERR_UNSUPPORTED = 7,  /* valid request this build does not implement */
+    DG_ERR_TIMEOUT = 8       /* a bounded device wait gave up */
+} dg_status;
+
+enum { DG_FP64 = 0, DG_FP32 = 1, DG_MIXED_FP16 = 2, DG_MIXED_BF16 = 3 };
+enum { DG_RUSANOV = 0, DG_ROE = 1 };
+enum { DG_ORDER_ASIS = 0, DG_ORDER_RCM = 1, DG_ORDER_MORTON = 2 };
+enum { DG_BC_INTERIOR = 0, DG_BC_WALL = 1, DG_BC_FARFIELD = 2 };
+
+typedef struct dg_mesh dg_mesh;   /* opaque; owns every device buffer it allocates */
+
+typedef struct {
+    int order;              /* polynomial order p: 1, 2 or 3 */
+    int precision;          /* DG_FP64 | DG_FP32 | DG_MIXED_FP16 | DG_MIXED_BF16 */
+    int flux;               /* DG_RUSANOV | DG_ROE */
+    double gamma;           /* ratio of specific heats, e.g. 1.4 */
+    int renumber;           /* DG_ORDER_ASIS | DG_ORDER_RCM | DG_ORDER_MORTON (Sec. III-B) */
+    double roe_entropy_eps; /* Harten fix on the acoustic speeds, delta = eps * c_hat; 0 = off */
+    double freestream[5];   /* conserved free-stream state for DG_BC_FARFIELD faces */
+} dg_config;
+
+/* Build a mesh: validates it, matches faces by sorted global vertex ids
+ * (periodic images share ids), derives orientations and affine geometry,
+ * optionally renumbers elements (Sec. III-B: RCM on the element adjacency
+ * graph; the paper does this once before time stepping), builds the basis and
+ * quadrature tables (Eq. 10, Sec. II-B) and uploads everything.
+ *   tet_vid [ne][4] int32: global vertex ids (topology).
+ *   tet_xyz [ne][4][3] FP64: unwrapped vertex coordinates of each tet
+ *           (geometry); det [x1-x0, x2-x0, x3-x0] must be > 0.
+ *   bc_tag  [ne][4] int8 per local face f (the face opposite local vertex f):
+ *           DG_BC_WALL or DG_BC_FARFIELD for faces with no partner; NULL when
+ *           every face is matched.  Tags of matched faces are ignored.
+ *   All three arrays are host memory, copied.  *out receives the mesh.
+ * Errors: DG_ERR_ARG, DG_ERR_MESH, DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_mesh_create(const int32_t* tet_vid, const double* tet_xyz, const int8_t* bc_tag,
+                         int64_t ne, const dg_config* cfg, void* stream, dg_mesh** out);
+
+/* Free the mesh and all its device memory (synchronises the device). */
+dg_status dg_mesh_destroy(dg_mesh* mesh);
+
+/* Mesh facts: number of distinct faces, of boundary faces, element-adjacency
+ * bandwidth max|i-j| before and after renumbering (the quantity of Tab. 1),
+ * and (if perm != NULL, host [ne]) the internal position of every caller
+ * element.  Any output pointer may be NULL. */
+dg_status dg_mesh_info(const dg_mesh* mesh, int64_t* n_faces, int64_t* n_bfaces,
+                       int64_t* bandwidth_before, int64_t* bandwidth_after, int32_t* perm);
+
+/* Sizes: Nb modes, Nq volume points, Nqf points per face. */
+dg_status dg_sizes(const dg_mesh* mesh, int* nb, int* nq, int* nqf);
+
+/* Physical coordinates of the volume quadrature points, host or device FP64
+ * [ne][Nq][3] in caller element order (for evaluating initial fields). */
+dg_status dg_volume_points(const dg_mesh* mesh, double* xyz, int on_device, void* stream);
+
+/* L2 projection (Eq. 10) of pointwise values f [ne][Nq][5] given at the
+ * points of dg_volume_points, by the volume rule: U_j = sum_q w_q f_q phi_j
+ * / sum_q w_q phi_j^2 (exact for polynomials of degree <= p).  f and U are
+ * FP64 in caller order, both on the host or both on the device. */
+dg_status dg_project(const dg_mesh* mesh, const double* f, double* U, int on_device, void* stream);
+
+/* Set / read the internal state (copied; caller order, FP64 [ne][5][Nb]).
+ * on_device selects host or device memory for U.  With a host U,
+ * dg_get_state synchronises the stream before it returns. */
+dg_status dg_set_state(dg_mesh* mesh, const double* U, int on_device, void* stream);
+dg_status dg_get_state(const dg_mesh* mesh, double* U, int on_device, void* stream);
+
+/* Residual R = M^-1 (volume - faces) of Eq. 11 (dU/dt of the semi-discrete
+ * system).  U: device FP64 [ne][5][Nb] in caller order, or NULL for the
+ * internal state; R: device FP64 [ne][5][Nb], caller-owned, caller order. */
+dg_status dg_residual(dg_mesh* mesh, const double* U, double* R, void* stream);
+
+/* One SSP-RK3 stage on the internal state, fused with the residual (one
+ * kernel launch): stage 1 U1 = U0 + dt R(U0); stage 2 U2 = 3/4 U0 + 1/4 (U1
+ * + dt R(U1)); stage 3 U0 <- 1/3 U0 + 2/3 (U2 + dt R(U2)). */
+dg_status dg_rk_stage(dg_mesh* mesh, int stage, double dt, void* stream);
+
+/* nsteps SSP-RK3 steps (3 stages each) on the internal state, in place. */
+dg_status dg_rk3_step(dg_mesh* mesh, double dt, int nsteps, void* stream);
+
+/* dt = cfl * min_e h_e / ((2p+1)(|u|_e + c_e)), h_e = 3 vol_e / max face
+ * area, from the element means of the internal state (Sec. III-C: local
+ * steps, then a deterministic two-pass minimum).  Synchronises the stream. */
+dg_status dg_stable_dt(dg_mesh* mesh, double cfl, double* dt_host, void* stream);
+
+/* Totals int U_v dx of the 5 conserved variables and the kinetic energy
+ * int |m|^2/(2 rho) dx (volume rule), FP64, fixed-order two-pass sums.  U:
+ * device FP64 caller order, or NULL for the internal state.  Synchronises. */
+dg_status dg_integrals(dg_mesh* mesh, const double* U, double totals[5], double* kinetic_energy,
+                       void* stream);
+
+/* Vector-Jacobian product out = (dR/dU)^T lambda of dg_residual at U (no
+ * counterpart in the paper).  U, lambda, out: device FP64 caller order. */
+dg_status dg_residual_vjp(dg_mesh* mesh, const double* U, const double* lambda, double* out,
+                          void* stream);
+
+/* out = (d U_{n+1} / d U_n)^T lambda for one SSP-RK3 step from U0 with step
+ * dt (stages recomputed).  Device FP64 caller order. */
+dg_status dg_rk3_step_vjp(dg_mesh* mesh, const double* U0, double dt, const double* lambda,
+                          double* out, void* stream);
+
+/* Synchronise the stream and return DG_ERR_NONPHYSICAL if any kernel since
+ * the last call flagged rho <= 0, p <= 0 or a non-finite value; clears the flag. */
+dg_status dg_sync_status(dg_mesh* mesh, void* stream);
+
+/* Host-only introspection of the reference element for order p (no device
+ * work, no mesh): volume rule (vol_xi [Nq][3], vol_w [Nq], weights sum to
+ * 1/6), face rule (face_bary [Nqf][3] barycentrics on a face's 3 vertices,
+ * face_w [Nqf], sum 1/2) and the basis at the volume points phi [Nq][Nb] and
+ * its reference gradient dphi [Nq][Nb][3].  Any output may be NULL. */
+dg_status dg_reference_data(int order, double* vol_xi, double* vol_w, double* face_bary, double* face_w,
+                            double* phi, double* dphi);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H */

@@ -216,20 +216,26 @@ class Problem:
         """x = x_0 + J xi for reference points X[n,3]: [ne, n, 3]."""
         return self.xyz[:, 0][:, None, :] + _es("edk,qk->eqd", self.J, X)
 
-    def project(self, field, nquad=None):
+    def project(self, field, nquad=None, rule="conical", elems=None):
         """L2 projection of field(x[...,3]) -> [...,5] onto the basis, with the
-        conical product rule of nquad points per direction (default p+3)."""
-        X, w = conical_tet_rule(nquad or self.p + 3)
+        conical product rule of nquad points per direction (default p+3), or
+        with the discretisation's own volume rule (rule="volume", cheaper);
+        for the elements ``elems`` only if given."""
+        if rule == "volume":
+            X, w = self.Xq, self.wq
+        else:
+            X, w = conical_tet_rule(nquad or self.p + 3)
         phi = eval_basis(self.p, X)[0]
-        out = np.empty((self.ne, 5, self.nb))
+        e_all = np.arange(self.ne) if elems is None else np.asarray(elems, dtype=np.int64)
+        out = np.empty((len(e_all), 5, self.nb))
         Mq = _es("q,qa,qb->ab", w, phi, phi)
-        for s in range(0, self.ne, CHUNK):
-            e = np.arange(s, min(s + CHUNK, self.ne))
+        for s in range(0, len(e_all), CHUNK):
+            e = e_all[s:s + CHUNK]
             x = self.xyz[e, 0][:, None, :] + _es("edk,qk->eqd", self.J[e], X)
             fx = field(x)
             b = _es("q,e,eqv,qj->ejv", w, self.det[e], fx, phi)
             M = self.det[e][:, None, None] * Mq[None]
-            out[e] = np.linalg.solve(M, b).transpose(0, 2, 1)
+            out[s:s + CHUNK] = np.linalg.solve(M, b).transpose(0, 2, 1)
         return out
 
     def l2_error(self, U, field, var=0, nquad=None):

@@ -43,31 +43,35 @@ def tet_monomial_integral(a: int, b: int, c: int) -> float:
     return math.factorial(a) * math.factorial(b) * math.factorial(c) / math.factorial(a + b + c + 3)
 
 
-def _unique_perms(t):
-    return sorted(set(itertools.permutations(t)))
+def _orbit(values, pattern):
+    """Distinct permutations of an index pattern, mapped to ``values`` (the
+    pattern, not the values, decides which points coincide, so the orbit can
+    be evaluated on any number type)."""
+    pats = sorted(set(itertools.permutations(pattern)))
+    return [tuple(values[i] for i in pat) for pat in pats]
 
 
 # orbit generators: parameters -> list of barycentric points
 def _tri_orbit(kind, prm):
     if kind == "S21":
         a = prm[0]
-        return _unique_perms((a, a, 1.0 - 2.0 * a))
+        return _orbit((a, 1.0 - 2.0 * a), (0, 0, 1))
     if kind == "S111":
         a, b = prm
-        return list(itertools.permutations((a, b, 1.0 - a - b)))
+        return _orbit((a, b, 1.0 - a - b), (0, 1, 2))
     raise ValueError(kind)
 
 
 def _tet_orbit(kind, prm):
     if kind == "S31":
         a = prm[0]
-        return _unique_perms((a, a, a, 1.0 - 3.0 * a))
+        return _orbit((a, 1.0 - 3.0 * a), (0, 0, 0, 1))
     if kind == "S22":
         a = prm[0]
-        return _unique_perms((a, a, 0.5 - a, 0.5 - a))
+        return _orbit((a, 0.5 - a), (0, 0, 1, 1))
     if kind == "S211":
         a, b = prm
-        return _unique_perms((a, a, b, 1.0 - 2.0 * a - b))
+        return _orbit((a, b, 1.0 - 2.0 * a - b), (0, 0, 1, 2))
     raise ValueError(kind)
 
 
@@ -99,6 +103,68 @@ def _assemble(orbits, x, orbit_fn):
     return np.array(pts, dtype=np.float64), np.array(wts, dtype=np.float64)
 
 
+def _refine(orbits, x, orbit_fn, monos, dim, iters=3):
+    """Gauss-Newton corrections with the moment residual evaluated in 40-digit
+    arithmetic (mpmath): some orbit parameters are fixed by the equations only
+    to ~1e-13 at double-precision residuals."""
+    import mpmath as mp
+    mp.mp.dps = 40
+    exact = [mp.factorial(m[0]) * mp.factorial(m[1]) * (mp.factorial(m[2]) if dim == 3 else 1)
+             / mp.factorial(sum(m) + dim) for m in monos]
+
+    def resid_mp(xm):
+        lam, w = [], []
+        k = 0
+        for kind, _ in orbits:
+            n = _NPARAM[kind]
+            o = orbit_fn(kind, xm[k:k + n])
+            lam.extend(o)
+            w.extend([xm[k + n]] * len(o))
+            k += n + 1
+        out = []
+        for m, ex in zip(monos, exact):
+            s = mp.mpf(0)
+            for l, wi in zip(lam, w):
+                t = wi
+                for d in range(dim):
+                    t *= l[d + 1] ** m[d]
+                s += t
+            out.append(s - ex)
+        return out
+
+    def jac(xd):
+        h = 1e-30
+        cols = []
+        for k in range(len(xd)):
+            xc = xd.astype(np.complex128)
+            xc[k] += 1j * h
+            lam, w = [], []
+            kk = 0
+            for kind, _ in orbits:
+                n = _NPARAM[kind]
+                o = orbit_fn(kind, list(xc[kk:kk + n]))
+                lam.extend(o)
+                w.extend([xc[kk + n]] * len(o))
+                kk += n + 1
+            lam = np.array(lam)
+            w = np.array(w)
+            col = []
+            for m in monos:
+                t = w.copy()
+                for d in range(dim):
+                    t = t * lam[:, d + 1] ** m[d]
+                col.append(np.sum(t).imag / h)
+            cols.append(col)
+        return np.array(cols).T
+
+    xm = [mp.mpf(float(v)) for v in x]
+    for _ in range(iters):
+        r = np.array([float(v) for v in resid_mp(xm)])
+        d = np.linalg.lstsq(jac(np.array([float(v) for v in xm])), -r, rcond=None)[0]
+        xm = [a + mp.mpf(float(b)) for a, b in zip(xm, d)]
+    return np.array([float(v) for v in xm])
+
+
 def _solve(orbits, degree, dim):
     orbit_fn = _tri_orbit if dim == 2 else _tet_orbit
     if dim == 2:
@@ -118,8 +184,9 @@ def _solve(orbits, degree, dim):
 
     x0 = np.concatenate([np.array(s, dtype=np.float64) for _, s in orbits])
     sol = least_squares(resid, x0, method="lm", xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=20000)
-    lam, w = _assemble(orbits, sol.x, orbit_fn)
-    err = np.max(np.abs(resid(sol.x)))
+    x = _refine(orbits, sol.x, orbit_fn, monos, dim)
+    lam, w = _assemble(orbits, x, orbit_fn)
+    err = np.max(np.abs(resid(x)))
     if err > 1e-14 or np.any(lam <= 0.0) or np.any(w <= 0.0):
         raise RuntimeError(f"quadrature solve failed: degree {degree}, dim {dim}, err {err}")
     return lam, w

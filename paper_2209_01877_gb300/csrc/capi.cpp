@@ -1,0 +1,381 @@
+// C ABI entry points (include/dg.h): argument checks, device buffers, and
+// the sequencing of kernel launches on the caller's stream.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "dg_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+dg_status fail(dg_status code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+dg_status cuda_fail(cudaError_t e, const char* where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+}
+
+#define DG_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+size_t real_size(int precision) { return precision == DG_FP64 ? sizeof(double) : sizeof(float); }
+
+template <typename T>
+dg_status upload(T** dst, const T* src, size_t n, cudaStream_t s) {
+    DG_CUDA(cudaMalloc(reinterpret_cast<void**>(dst), n * sizeof(T) + 16));
+    DG_CUDA(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, s));
+    return DG_OK;
+}
+
+void free_mesh(dg_mesh* m) {
+    if (!m) return;
+    cudaFree(m->d_nbr);
+    cudaFree(m->d_fcode);
+    cudaFree(m->d_perm);
+    cudaFree(m->d_jinv);
+    cudaFree(m->d_jinv64);
+    cudaFree(m->d_tab);
+    cudaFree(m->d_tab64);
+    cudaFree(m->d_fperm);
+    for (auto& b : m->d_B) cudaFree(b);
+    cudaFree(m->d_io);
+    cudaFree(m->d_red);
+    cudaFree(m->d_status);
+    if (m->h_red) cudaFreeHost(m->h_red);
+    delete m;
+}
+
+constexpr int RED_SLOTS = 1024 * 6;   // per-block partials; results follow
+
+}  // namespace
+
+size_t dg_mesh::state_bytes() const { return (size_t)host.ne * 5 * nb * real_size(precision); }
+
+extern "C" {
+
+const char* dg_last_error(void) { return g_err.c_str(); }
+
+dg_status dg_mesh_create(const int32_t* tet_vid, const double* tet_xyz, const int8_t* bc_tag, int64_t ne,
+                         const dg_config* cfg, void* stream, dg_mesh** out) {
+    g_err.clear();
+    if (!out) return fail(DG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!tet_vid || !tet_xyz || !cfg) return fail(DG_ERR_ARG, "tet_vid, tet_xyz and cfg must be non-NULL");
+    if (ne <= 0 || ne > (int64_t)INT32_MAX / 4) return fail(DG_ERR_ARG, "ne out of range");
+    if (cfg->order < 1 || cfg->order > 3) return fail(DG_ERR_ARG, "order must be 1, 2 or 3");
+    if (cfg->precision < DG_FP64 || cfg->precision > DG_MIXED_BF16) return fail(DG_ERR_ARG, "bad precision");
+    if (cfg->precision == DG_MIXED_FP16 || cfg->precision == DG_MIXED_BF16)
+        return fail(DG_ERR_UNSUPPORTED, "mixed precision is not available in this build");
+    if (cfg->flux != DG_RUSANOV && cfg->flux != DG_ROE) return fail(DG_ERR_ARG, "bad flux");
+    if (!(cfg->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must exceed 1");
+    if (cfg->renumber < DG_ORDER_ASIS || cfg->renumber > DG_ORDER_MORTON) return fail(DG_ERR_ARG, "bad renumber");
+    if (!(cfg->roe_entropy_eps >= 0.0)) return fail(DG_ERR_ARG, "roe_entropy_eps must be >= 0");
+
+    dg_mesh* m = new dg_mesh();
+    m->p = cfg->order;
+    m->nb = dg::nb_of(m->p);
+    m->nq = dg::nq_of(m->p);
+    m->nqf = dg::nqf_of(m->p);
+    m->precision = cfg->precision;
+    m->flux = cfg->flux;
+    m->gamma = cfg->gamma;
+    m->roe_eps = cfg->roe_entropy_eps;
+    for (int v = 0; v < 5; ++v) m->finf[v] = cfg->freestream[v];
+
+    int code = DG_OK;
+    std::string err;
+    if (!dg::build_mesh(tet_vid, tet_xyz, bc_tag, ne, cfg->renumber, m->host, code, err)) {
+        free_mesh(m);
+        return fail((dg_status)code, err);
+    }
+    m->has_bc = m->host.n_bfaces > 0;
+    bool farfield = false;
+    for (int32_t n : m->host.nbr) farfield |= (n == -1 - DG_BC_FARFIELD);
+    if (farfield && !(cfg->freestream[0] > 0.0)) {
+        free_mesh(m);
+        return fail(DG_ERR_ARG, "far-field faces need a free-stream state with positive density");
+    }
+    if (!dg::build_reference(m->p, m->ref, err)) {
+        free_mesh(m);
+        return fail(DG_ERR_ARG, err);
+    }
+    cudaStream_t s = as_stream(stream);
+    dg_status st = DG_OK;
+#define DG_TRY(x)                      \
+    do {                               \
+        st = (x);                      \
+        if (st != DG_OK) {             \
+            free_mesh(m);              \
+            return st;                 \
+        }                              \
+    } while (0)
+    {
+        cudaError_t e = cudaGetDevice(&m->device);
+        if (e != cudaSuccess) { free_mesh(m); return cuda_fail(e, "cudaGetDevice"); }
+    }
+    DG_TRY(upload(&m->d_nbr, m->host.nbr.data(), m->host.nbr.size(), s));
+    DG_TRY(upload(&m->d_fcode, m->host.fcode.data(), m->host.fcode.size(), s));
+    DG_TRY(upload(&m->d_perm, m->host.perm.data(), m->host.perm.size(), s));
+    DG_TRY(upload(&m->d_jinv64, m->host.jinv.data(), m->host.jinv.size(), s));
+    DG_TRY(upload(&m->d_fperm, m->ref.fperm.data(), m->ref.fperm.size(), s));
+    // FP64 tables followed by the volume points' reference coordinates
+    std::vector<double> tab64 = m->ref.tab;
+    tab64.insert(tab64.end(), m->ref.vol_xi.begin(), m->ref.vol_xi.end());
+    DG_TRY(upload(&m->d_tab64, tab64.data(), tab64.size(), s));
+    std::vector<float> tab32(m->ref.tab.begin(), m->ref.tab.end());
+    std::vector<float> jinv32(m->host.jinv.begin(), m->host.jinv.end());
+    if (m->precision == DG_FP64) {
+        m->d_tab = m->d_tab64;   // shared; freed once below
+        m->d_jinv = m->d_jinv64;
+    } else {
+        float* t = nullptr;
+        DG_TRY(upload(&t, tab32.data(), tab32.size(), s));
+        m->d_tab = t;
+        float* j = nullptr;
+        DG_TRY(upload(&j, jinv32.data(), jinv32.size(), s));
+        m->d_jinv = j;
+    }
+    for (auto& b : m->d_B) {
+        cudaError_t e = cudaMalloc(&b, m->state_bytes() + 256);
+        if (e != cudaSuccess) { free_mesh(m); return cuda_fail(e, "cudaMalloc(state)"); }
+    }
+    {
+        cudaError_t e = cudaMalloc(&m->d_red, (RED_SLOTS + 16) * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&m->d_status, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->d_status, 0, sizeof(unsigned int), s);
+        if (e == cudaSuccess) e = cudaMallocHost(&m->h_red, 16 * sizeof(double));
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { free_mesh(m); return cuda_fail(e, "mesh buffers"); }
+    }
+    *out = m;
+    return DG_OK;
+#undef DG_TRY
+}
+
+dg_status dg_mesh_destroy(dg_mesh* m) {
+    if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
+    cudaDeviceSynchronize();
+    if (m->d_tab == m->d_tab64) m->d_tab = nullptr;
+    if (m->d_jinv == m->d_jinv64) m->d_jinv = nullptr;
+    free_mesh(m);
+    return DG_OK;
+}
+
+dg_status dg_mesh_info(const dg_mesh* m, int64_t* n_faces, int64_t* n_bfaces, int64_t* bw_before,
+                       int64_t* bw_after, int32_t* perm) {
+    if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
+    if (n_faces) *n_faces = m->host.n_faces;
+    if (n_bfaces) *n_bfaces = m->host.n_bfaces;
+    if (bw_before) *bw_before = m->host.bw_before;
+    if (bw_after) *bw_after = m->host.bw_after;
+    if (perm) std::memcpy(perm, m->host.iperm.data(), m->host.iperm.size() * sizeof(int32_t));
+    return DG_OK;
+}
+
+dg_status dg_sizes(const dg_mesh* m, int* nb, int* nq, int* nqf) {
+    if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
+    if (nb) *nb = m->nb;
+    if (nq) *nq = m->nq;
+    if (nqf) *nqf = m->nqf;
+    return DG_OK;
+}
+
+dg_status dg_volume_points(const dg_mesh* mc, double* xyz, int on_device, void* stream) {
+    dg_mesh* m = const_cast<dg_mesh*>(mc);
+    if (!m || !xyz) return fail(DG_ERR_ARG, "mesh and xyz must be non-NULL");
+    cudaStream_t s = as_stream(stream);
+    double* d_x0J = nullptr;
+    double* d_out = on_device ? xyz : nullptr;
+    const size_t nout = (size_t)m->host.ne * m->nq * 3;
+    DG_CUDA(cudaMalloc(&d_x0J, m->host.x0J.size() * sizeof(double)));
+    cudaError_t e = cudaMemcpyAsync(d_x0J, m->host.x0J.data(), m->host.x0J.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !on_device) e = cudaMalloc(&d_out, nout * sizeof(double));
+    if (e == cudaSuccess) e = dg::launch_volume_points(m, d_x0J, d_out, s);
+    if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(xyz, d_out, nout * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_x0J);
+    if (!on_device) cudaFree(d_out);
+    if (e != cudaSuccess) return cuda_fail(e, "dg_volume_points");
+    return DG_OK;
+}
+
+dg_status dg_project(const dg_mesh* mc, const double* f, double* U, int on_device, void* stream) {
+    dg_mesh* m = const_cast<dg_mesh*>(mc);
+    if (!m || !f || !U) return fail(DG_ERR_ARG, "mesh, f and U must be non-NULL");
+    cudaStream_t s = as_stream(stream);
+    if (on_device) {
+        DG_CUDA(dg::launch_project(m, f, U, s));
+        return DG_OK;
+    }
+    const size_t nf = (size_t)m->host.ne * m->nq * 5, nu = (size_t)m->host.ne * 5 * m->nb;
+    double *df = nullptr, *du = nullptr;
+    cudaError_t e = cudaMalloc(&df, nf * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&du, nu * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(df, f, nf * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = dg::launch_project(m, df, du, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(U, du, nu * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(df);
+    cudaFree(du);
+    if (e != cudaSuccess) return cuda_fail(e, "dg_project");
+    return DG_OK;
+}
+
+dg_status dg_set_state(dg_mesh* m, const double* U, int on_device, void* stream) {
+    if (!m || !U) return fail(DG_ERR_ARG, "mesh and U must be non-NULL");
+    cudaStream_t s = as_stream(stream);
+    const double* src = U;
+    if (!on_device) {
+        if (!m->d_io) DG_CUDA(cudaMalloc(&m->d_io, (size_t)m->host.ne * 5 * m->nb * sizeof(double)));
+        DG_CUDA(cudaMemcpyAsync(m->d_io, U, (size_t)m->host.ne * 5 * m->nb * sizeof(double), cudaMemcpyHostToDevice, s));
+        src = m->d_io;
+    }
+    DG_CUDA(dg::launch_gather(m, src, m->d_B[0], s));
+    m->has_state = true;
+    return DG_OK;
+}
+
+dg_status dg_get_state(const dg_mesh* mc, double* U, int on_device, void* stream) {
+    dg_mesh* m = const_cast<dg_mesh*>(mc);
+    if (!m || !U) return fail(DG_ERR_ARG, "mesh and U must be non-NULL");
+    if (!m->has_state) return fail(DG_ERR_NOSTATE, "no state set");
+    cudaStream_t s = as_stream(stream);
+    if (on_device) {
+        DG_CUDA(dg::launch_scatter(m, m->d_B[0], U, s));
+        return DG_OK;
+    }
+    if (!m->d_io) DG_CUDA(cudaMalloc(&m->d_io, (size_t)m->host.ne * 5 * m->nb * sizeof(double)));
+    DG_CUDA(dg::launch_scatter(m, m->d_B[0], m->d_io, s));
+    DG_CUDA(cudaMemcpyAsync(U, m->d_io, (size_t)m->host.ne * 5 * m->nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    return DG_OK;
+}
+
+dg_status dg_residual(dg_mesh* m, const double* U, double* R, void* stream) {
+    if (!m || !R) return fail(DG_ERR_ARG, "mesh and R must be non-NULL");
+    cudaStream_t s = as_stream(stream);
+    const void* in = m->d_B[0];
+    if (U) {
+        DG_CUDA(dg::launch_gather(m, U, m->d_B[1], s));
+        in = m->d_B[1];
+    } else if (!m->has_state) {
+        return fail(DG_ERR_NOSTATE, "no state set and U is NULL");
+    }
+    DG_CUDA(dg::launch_residual(m, in, nullptr, m->d_B[2], 0, 0.0, 0.0, 0.0, s));
+    DG_CUDA(dg::launch_scatter(m, m->d_B[2], R, s));
+    return DG_OK;
+}
+
+dg_status dg_rk_stage(dg_mesh* m, int stage, double dt, void* stream) {
+    if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
+    if (!m->has_state) return fail(DG_ERR_NOSTATE, "no state set");
+    if (!(dt >= 0.0)) return fail(DG_ERR_ARG, "dt must be >= 0");
+    cudaStream_t s = as_stream(stream);
+    void** B = m->d_B;
+    switch (stage) {
+        case 1: DG_CUDA(dg::launch_residual(m, B[0], nullptr, B[1], 1, dt, 0.0, 1.0, s)); break;
+        case 2: DG_CUDA(dg::launch_residual(m, B[1], B[0], B[2], 1, dt, 0.75, 0.25, s)); break;
+        case 3: DG_CUDA(dg::launch_residual(m, B[2], B[0], B[0], 1, dt, 1.0 / 3.0, 2.0 / 3.0, s)); break;
+        default: return fail(DG_ERR_ARG, "stage must be 1, 2 or 3");
+    }
+    return DG_OK;
+}
+
+dg_status dg_rk3_step(dg_mesh* m, double dt, int nsteps, void* stream) {
+    if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
+    if (nsteps < 0) return fail(DG_ERR_ARG, "nsteps must be >= 0");
+    for (int n = 0; n < nsteps; ++n)
+        for (int st = 1; st <= 3; ++st) {
+            dg_status r = dg_rk_stage(m, st, dt, stream);
+            if (r != DG_OK) return r;
+        }
+    return DG_OK;
+}
+
+dg_status dg_stable_dt(dg_mesh* m, double cfl, double* dt_host, void* stream) {
+    if (!m || !dt_host) return fail(DG_ERR_ARG, "mesh and dt_host must be non-NULL");
+    if (!m->has_state) return fail(DG_ERR_NOSTATE, "no state set");
+    if (!(cfl > 0.0)) return fail(DG_ERR_ARG, "cfl must be positive");
+    cudaStream_t s = as_stream(stream);
+    double* d_out = m->d_red + RED_SLOTS;
+    DG_CUDA(dg::launch_stable_dt(m, m->d_B[0], d_out, s));
+    DG_CUDA(cudaMemcpyAsync(m->h_red, d_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    *dt_host = cfl * m->h_red[0];
+    return DG_OK;
+}
+
+dg_status dg_integrals(dg_mesh* m, const double* U, double totals[5], double* ke, void* stream) {
+    if (!m || !totals) return fail(DG_ERR_ARG, "mesh and totals must be non-NULL");
+    cudaStream_t s = as_stream(stream);
+    const void* in = m->d_B[0];
+    if (U) {
+        DG_CUDA(dg::launch_gather(m, U, m->d_B[1], s));
+        in = m->d_B[1];
+    } else if (!m->has_state) {
+        return fail(DG_ERR_NOSTATE, "no state set and U is NULL");
+    }
+    double* d_out = m->d_red + RED_SLOTS;
+    DG_CUDA(dg::launch_integrals(m, in, d_out, s));
+    DG_CUDA(cudaMemcpyAsync(m->h_red, d_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    for (int v = 0; v < 5; ++v) totals[v] = m->h_red[v];
+    if (ke) *ke = m->h_red[5];
+    return DG_OK;
+}
+
+dg_status dg_residual_vjp(dg_mesh* m, const double* U, const double* lambda, double* out, void* stream) {
+    (void)U; (void)lambda; (void)out; (void)stream;
+    if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
+    return fail(DG_ERR_UNSUPPORTED, "the adjoint is not available in this build");
+}
+
+dg_status dg_rk3_step_vjp(dg_mesh* m, const double* U0, double dt, const double* lambda, double* out, void* stream) {
+    (void)U0; (void)dt; (void)lambda; (void)out; (void)stream;
+    if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
+    return fail(DG_ERR_UNSUPPORTED, "the adjoint is not available in this build");
+}
+
+dg_status dg_reference_data(int order, double* vol_xi, double* vol_w, double* face_bary, double* face_w,
+                            double* phi, double* dphi) {
+    dg::RefData ref;
+    std::string err;
+    if (!dg::build_reference(order, ref, err)) return fail(DG_ERR_ARG, err);
+    const int nq = dg::nq_of(order), nqf = dg::nqf_of(order), nb = dg::nb_of(order);
+    if (vol_xi) std::memcpy(vol_xi, ref.vol_xi.data(), 3 * nq * sizeof(double));
+    if (vol_w) std::memcpy(vol_w, ref.vol_w.data(), nq * sizeof(double));
+    if (face_bary) std::memcpy(face_bary, ref.face_bary.data(), 3 * nqf * sizeof(double));
+    if (face_w) std::memcpy(face_w, ref.face_w.data(), nqf * sizeof(double));
+    std::vector<double> ph(nb), gr(3 * nb);
+    for (int q = 0; q < nq; ++q) {
+        dg::eval_basis(order, &ref.vol_xi[3 * q], ph.data(), gr.data());
+        if (phi) std::memcpy(phi + (size_t)q * nb, ph.data(), nb * sizeof(double));
+        if (dphi) std::memcpy(dphi + (size_t)q * nb * 3, gr.data(), 3 * nb * sizeof(double));
+    }
+    return DG_OK;
+}
+
+dg_status dg_sync_status(dg_mesh* m, void* stream) {
+    if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
+    cudaStream_t s = as_stream(stream);
+    unsigned int flag = 0;
+    DG_CUDA(cudaMemcpyAsync(&flag, m->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    DG_CUDA(cudaMemsetAsync(m->d_status, 0, sizeof(unsigned int), s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    if (flag & 1u) return fail(DG_ERR_NONPHYSICAL, "non-positive density or pressure (or non-finite value) seen on the device");
+    return DG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// Internal declarations shared by the host code (C++) and the kernels (CUDA).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dg.h"
+
+namespace dg {
+
+// Sizes per polynomial order p (1..3): modes, volume points (symmetric rule
+// exact to degree 2p), face points (symmetric triangle rule exact to 2p).
+constexpr int nb_of(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+constexpr int nq_of(int p) { return p == 1 ? 4 : (p == 2 ? 14 : 24); }
+constexpr int nqf_of(int p) { return p == 1 ? 3 : (p == 2 ? 6 : 12); }
+
+// Offsets (in elements of the table's scalar type) of the basis tables,
+// stored contiguously so a kernel can stage them into shared memory at once:
+//   PHIQ  [Nb][Nq]      phi_j at volume point q
+//   DPHIW [3][Nq][Nb]   w_q * d phi_j / d xi_k at volume point q
+//   PHIF  [4][Nb][Nqf]  phi_j at point q of local face f (own point order)
+//   PHIFW [4][Nqf][Nb]  wf_q * phi_j at point q of local face f
+//   WQ    [Nq]          volume weights (sum 1/6)
+struct TabLayout {
+    int nb, nq, nqf;
+    int phiq, dphiw, phif, phifw, wq, total;
+    explicit TabLayout(int p) {
+        nb = nb_of(p); nq = nq_of(p); nqf = nqf_of(p);
+        phiq = 0;
+        dphiw = phiq + nb * nq;
+        phif = dphiw + 3 * nq * nb;
+        phifw = phif + 4 * nb * nqf;
+        wq = phifw + 4 * nqf * nb;
+        total = wq + nq;
+    }
+};
+
+// Host-built reference data (FP64): quadrature, basis tables and the face
+// point permutations for the 6 relative orientations.
+struct RefData {
+    int p = 0;
+    std::vector<double> vol_xi;    // [Nq][3] reference coordinates
+    std::vector<double> vol_w;     // [Nq]
+    std::vector<double> face_bary; // [Nqf][3] barycentrics on the face's 3 vertices
+    std::vector<double> face_w;    // [Nqf]
+    std::vector<double> tab;       // TabLayout(p).total values
+    std::vector<int8_t> fperm;     // [6][Nqf]
+};
+
+bool build_reference(int p, RefData& out, std::string& err);
+void eval_basis(int p, const double xi[3], double* phi, double* grad /* [Nb][3] or null */);
+extern const int kPerm3[6][3];     // the 6 permutations of (0,1,2), indexed by orientation code
+
+// Face code of an interior (element, local face): bits 0-1 the neighbour's
+// local face, bits 2-4 the orientation code.  Boundary faces store the
+// negative neighbour id -1 - bc_type instead.
+struct MeshHost {
+    int64_t ne = 0, n_faces = 0, n_bfaces = 0, bw_before = 0, bw_after = 0;
+    std::vector<int32_t> perm;     // perm[internal] = caller index
+    std::vector<int32_t> iperm;    // iperm[caller] = internal index
+    std::vector<int32_t> nbr;      // [ne][4] internal order
+    std::vector<uint8_t> fcode;    // [ne][4]
+    std::vector<double> jinv;      // [ne][9] internal order, row-major J^-1
+    std::vector<double> x0J;       // [ne][12] caller order: x0 (3) then J row-major (9)
+};
+
+bool build_mesh(const int32_t* tet_vid, const double* tet_xyz, const int8_t* bc_tag, int64_t ne,
+                int renumber, MeshHost& out, int& code, std::string& err);
+
+}  // namespace dg
+
+// Device-side arguments of the residual / RK-stage kernel.
+template <typename Real>
+struct ResArgs {
+    const Real* U;         // residual input [ne][5][Nb] internal order
+    const Real* U0;        // RK base state (stages 2, 3)
+    Real* out;             // residual or new state
+    const int32_t* nbr;    // [ne][4]
+    const uint8_t* fcode;  // [ne][4]
+    const Real* jinv;      // [ne][9]
+    const Real* tab;       // basis tables (TabLayout)
+    const int8_t* fperm;   // [6][Nqf]
+    int64_t ne;
+    Real dt, a, b;         // out = a*U0 + b*(U + dt*R) in RK mode
+    Real gamma, roe_eps;
+    Real finf[5];          // free-stream conserved state
+    unsigned int* status;  // device status word
+};
+
+struct dg_mesh {
+    int p = 1, nb = 4, nq = 4, nqf = 3;
+    int precision = DG_FP64, flux = DG_RUSANOV;
+    double gamma = 1.4, roe_eps = 0.0, finf[5] = {0, 0, 0, 0, 0};
+    int device = 0;
+    bool has_bc = false, has_state = false;
+    dg::MeshHost host;
+    dg::RefData ref;
+    // device buffers
+    int32_t* d_nbr = nullptr;
+    uint8_t* d_fcode = nullptr;
+    int32_t* d_perm = nullptr;     // internal -> caller
+    void* d_jinv = nullptr;        // Real [ne][9]
+    double* d_jinv64 = nullptr;    // FP64 copy for reductions
+    void* d_tab = nullptr;         // Real tables
+    double* d_tab64 = nullptr;     // FP64 tables (projection, integrals)
+    int8_t* d_fperm = nullptr;
+    void* d_B[3] = {nullptr, nullptr, nullptr};   // state buffers (internal precision)
+    double* d_io = nullptr;        // FP64 [ne][5][Nb] staging for host copies
+    double* d_red = nullptr;       // reduction scratch
+    double* h_red = nullptr;       // pinned host reduction result
+    unsigned int* d_status = nullptr;
+    size_t state_bytes() const;
+};
+
+// Launchers (kernels.cu).  All return a cudaError_t of the launch.
+namespace dg {
+cudaError_t launch_residual(dg_mesh* m, const void* U, const void* U0, void* out, int mode,
+                            double dt, double a, double b, cudaStream_t s);
+cudaError_t launch_gather(dg_mesh* m, const double* user, void* internal, cudaStream_t s);   // caller -> internal
+cudaError_t launch_scatter(dg_mesh* m, const void* internal, double* user, cudaStream_t s);  // internal -> caller
+cudaError_t launch_stable_dt(dg_mesh* m, const void* U, double* d_out, cudaStream_t s);
+cudaError_t launch_integrals(dg_mesh* m, const void* U, double* d_out6, cudaStream_t s);
+cudaError_t launch_project(dg_mesh* m, const double* f, double* U, cudaStream_t s);
+cudaError_t launch_volume_points(dg_mesh* m, const double* d_x0J, double* xyz, cudaStream_t s);
+cudaError_t prepare_kernels(dg_mesh* m);
+}  // namespace dg

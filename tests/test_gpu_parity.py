@@ -1,0 +1,218 @@
+"""GPU parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance (FP64 path): per conserved quantity Q (mass, momentum as one
+vector quantity, energy),
+  max |R_gpu - R_oracle| <= 1e-12 * max |R_oracle[Q]|
+(a relative bar normalised by the quantity's largest residual, since a
+pointwise relative error is undefined where R ~ 0; the momentum components
+share one scale so that a component whose residual is small only because of
+the flow direction is not held to a tighter absolute bar than the others).  FP32 path: 2e-5 of the
+same scale (FP32 unit roundoff 6e-8 times the ~100 accumulated products of the
+P3 contractions, plus the conditioning of the face and volume cancellation).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.dg import Problem
+from paper_2209_01877_gb300 import dg
+from paper_2209_01877_gb300 import inputs as I
+
+from gpu_helpers import gpu_residual, make_mesh, max_rel_err, sample_elements, torch_cuda, vortex_state
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+
+def _box(nx=4, ny=3, nz=3):
+    return I.make_box_channel(nx, ny, nz, lengths=(2.0, 1.0, 1.0), jitter=0.15)
+
+
+def _box_state(P):
+    c = (0.9, 0.5, 0.5)
+
+    def field(x):
+        U = I.gaussian_pulse(x, c, width=0.3)
+        U[..., 2] += 0.05 * U[..., 0]
+        return U
+    return P.project(field)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("flux", ["rusanov", "roe"])
+def test_residual_periodic_fp64(p, flux):
+    m = I.make_periodic_cube(4, jitter=0.15)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=p, flux=flux)
+    U = vortex_state(P, radius=0.15)
+    R = P.residual(U)
+    M = make_mesh(m, p, flux)
+    assert max_rel_err(gpu_residual(M, U), R) < TOL64
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("flux", ["rusanov", "roe"])
+def test_residual_box_boundaries_fp64(p, flux):
+    m = _box()
+    Uinf = I.freestream_state(0.3)
+    P = Problem(m.tet_vid, m.tet_xyz, m.bc_tag, p=p, flux=flux, freestream=Uinf)
+    U = _box_state(P)
+    R = P.residual(U)
+    M = make_mesh(m, p, flux, freestream=Uinf)
+    assert M.info()["n_bfaces"] == 4 * (3 * 3 + 4 * 3 + 4 * 3)
+    assert max_rel_err(gpu_residual(M, U), R) < TOL64
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_residual_fp32(p):
+    m = I.make_periodic_cube(4, jitter=0.15)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=p, flux="roe")
+    U = vortex_state(P, radius=0.15)
+    R = P.residual(U)
+    M = make_mesh(m, p, "roe", precision="fp32")
+    assert max_rel_err(gpu_residual(M, U), R) < TOL32
+
+
+def test_renumbering_is_a_permutation():
+    """The residual in caller order is bitwise identical for every element order."""
+    m = I.make_periodic_cube(5, jitter=0.15)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=2, flux="roe")
+    U = vortex_state(P, radius=0.15)
+    out = [gpu_residual(make_mesh(m, 2, "roe", renumber=r), U)
+           for r in (dg.DG_ORDER_ASIS, dg.DG_ORDER_RCM, dg.DG_ORDER_MORTON)]
+    np.testing.assert_array_equal(out[0], out[1])
+    np.testing.assert_array_equal(out[0], out[2])
+    info = make_mesh(m, 2, "roe").info()
+    assert info["bandwidth_after"] < info["bandwidth_before"] / 4
+    perm = info["perm"]
+    assert sorted(perm.tolist()) == list(range(m.ne))
+
+
+def test_free_stream_and_conservation_gpu():
+    m = I.make_periodic_cube(4, jitter=0.15)
+    for p in (1, 2, 3):
+        P = Problem(m.tet_vid, m.tet_xyz, None, p=p)
+        M = make_mesh(m, p, "roe")
+        R = gpu_residual(M, P.project(I.uniform_flow))
+        assert np.abs(R).max() < 1e-11
+        R = gpu_residual(M, vortex_state(P, radius=0.15))
+        rate = np.einsum("e,ev->v", P.det, R[:, :, 0]) * math.sqrt(6.0) / 6.0
+        scale = np.einsum("e,ev->v", P.det, np.abs(R[:, :, 0]))
+        assert np.all(np.abs(rate) < 1e-13 * scale)
+
+
+def test_config1_one_rk3_step():
+    """6^3 x 6 periodic cube, jitter 10%, P1, isentropic vortex, Rusanov, one
+    SSP-RK3 step with dt from CFL 0.1."""
+    torch = torch_cuda()
+    m = I.make_periodic_cube(6, jitter=0.10)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=1, flux="rusanov")
+    U0 = vortex_state(P)
+    M = make_mesh(m, 1, "rusanov")
+    dg.dg_set_state(M.handle, U0)
+    dt_gpu = dg.dg_stable_dt(M.handle, 0.1)
+    dt = P.stable_dt(U0, 0.1)
+    assert abs(dt_gpu - dt) < 1e-14 * dt
+    dg.dg_rk3_step(M.handle, dt, 1)
+    U1 = np.empty_like(U0)
+    dg.dg_get_state(M.handle, U1)
+    dg.dg_sync_status(M.handle)
+    ref = P.rk3_step(U0, dt)
+    assert max_rel_err(U1 - U0, ref - U0) < 1e-11
+    assert max_rel_err(U1, ref) < 1e-14
+
+
+def test_state_roundtrip_and_integrals():
+    torch = torch_cuda()
+    m = I.make_periodic_cube(4, jitter=0.15)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=3)
+    U = vortex_state(P, radius=0.15)
+    M = make_mesh(m, 3, "roe")
+    dg.dg_set_state(M.handle, U)
+    back = np.empty_like(U)
+    dg.dg_get_state(M.handle, back)
+    np.testing.assert_array_equal(back, U)
+    tot, ke = dg.dg_integrals(M.handle)
+    tot_o, ke_o = P.integrals(U)
+    np.testing.assert_allclose(tot, tot_o, rtol=1e-13, atol=1e-15)
+    assert abs(ke - ke_o) < 1e-13 * abs(ke_o)
+    # device-array forms of the same calls
+    Ud = torch.from_numpy(U).cuda()
+    tot2, ke2 = dg.dg_integrals(M.handle, Ud)
+    np.testing.assert_array_equal(tot2, tot)
+
+
+def test_library_projection_matches_oracle_volume_rule():
+    m = I.make_periodic_cube(3, jitter=0.15)
+    for p in (1, 2, 3):
+        P = Problem(m.tet_vid, m.tet_xyz, None, p=p)
+        M = make_mesh(m, p)
+        f = lambda x: I.isentropic_vortex(x, radius=0.2)
+        np.testing.assert_allclose(M.project(f), P.project(f, rule="volume"), atol=1e-13, rtol=0)
+
+
+def test_nonphysical_state_is_reported():
+    m = I.make_periodic_cube(3, jitter=0.15)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=1)
+    U = P.project(I.uniform_flow)
+    U[7, 0, :] *= -1.0                       # negative density in one element
+    M = make_mesh(m, 1)
+    torch = torch_cuda()
+    Ud = torch.from_numpy(U).cuda()
+    R = torch.empty_like(Ud)
+    dg.dg_residual(M.handle, Ud, R)
+    with pytest.raises(dg.DGError) as e:
+        dg.dg_sync_status(M.handle)
+    assert e.value.status == 5
+    dg.dg_sync_status(M.handle)              # the flag was cleared
+
+
+def test_rk3_many_steps_fp64_matches_oracle():
+    m = I.make_periodic_cube(3, jitter=0.15)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=2, flux="roe")
+    U0 = vortex_state(P, radius=0.2)
+    dt = P.stable_dt(U0, 0.2)
+    M = make_mesh(m, 2, "roe")
+    dg.dg_set_state(M.handle, U0)
+    dg.dg_rk3_step(M.handle, dt, 10)
+    U = np.empty_like(U0)
+    dg.dg_get_state(M.handle, U)
+    ref = P.rk3(U0, dt, 10)
+    assert max_rel_err(U - U0, ref - U0) < 1e-10
+
+
+# ---- full-size workloads, sampled -----------------------------------------------------------
+def _sampled(m, p, flux, U_fn, freestream=None, nsample=1500, precision="fp64", include=()):
+    P = Problem(m.tet_vid, m.tet_xyz, m.bc_tag if not all(m.periodic) else None, p=p, flux=flux,
+                freestream=freestream)
+    U = U_fn(P)
+    M = make_mesh(m, p, flux, precision=precision, freestream=freestream)
+    R = gpu_residual(M, U)
+    rows = sample_elements(m.ne, nsample, include=include)
+    ref = P.residual(U, rows)
+    return max_rel_err(R[rows], ref)
+
+
+@pytest.mark.slow
+def test_full_size_p2_48cube_fp64_and_fp32():
+    m = I.make_periodic_cube(48, jitter=0.10)
+    U_fn = lambda P: vortex_state(P, perturb=True, rule="volume")
+    assert _sampled(m, 2, "rusanov", U_fn) < TOL64
+    assert _sampled(m, 2, "rusanov", U_fn, precision="fp32") < TOL32
+
+
+@pytest.mark.slow
+def test_full_size_p3_64cube_roe_fp64():
+    m = I.make_periodic_cube(64, jitter=0.15)
+    assert _sampled(m, 3, "roe", lambda P: vortex_state(P, rule="volume")) < TOL64
+
+
+@pytest.mark.slow
+def test_full_size_p3_box_channel_fp64():
+    m = I.make_box_channel(96, 48, 48, jitter=0.15)
+    Uinf = I.freestream_state(0.3)
+    c = I.pulse_centre()
+    bnd = np.nonzero(np.any(m.bc_tag > 0, axis=1))[0][:300]
+    U_fn = lambda P: P.project(lambda x: I.gaussian_pulse(x, c), rule="volume")
+    assert _sampled(m, 3, "roe", U_fn, freestream=Uinf, include=bnd) < TOL64
