@@ -137,15 +137,25 @@ dg_status dg_stable_dt(dg_mesh* mesh, double cfl, double* dt_host, void* stream)
 dg_status dg_integrals(dg_mesh* mesh, const double* U, double totals[5], double* kinetic_energy,
                        void* stream);
 
-/* Vector-Jacobian product out = (dR/dU)^T lambda of dg_residual at U (no
- * counterpart in the paper).  U, lambda, out: device FP64 caller order. */
-dg_status dg_residual_vjp(dg_mesh* mesh, const double* U, const double* lambda, double* out,
+/* Vector-Jacobian product out = (dR/dU)^T lambda of dg_residual at U (the
+ * paper has no adjoint; this reverses the steps of Eq. 11's discretisation:
+ * inverse mass, projection, pointwise flux and Riemann-solver Jacobians,
+ * interpolation, on both sides of every face; at a kink of |.| or max the
+ * derivative of the branch taken, ties to the interior side).  U, lambda,
+ * out: device FP64 [ne][5][Nb] in caller order. */
+dg_status dg_residual_vjp(dg_mesh* mesh, const double* U, const double* lambda, double* out, void* stream);
+
+/* out = (d U_{n+1} / d U_n)^T lambda for one SSP-RK3 step of size dt from
+ * U0 (stages recomputed): m2 = 2/3 (lambda + dt J(U2)^T lambda),
+ * m1 = 1/4 (m2 + dt J(U1)^T m2), out = lambda/3 + 3/4 m2 + m1 + dt J(U0)^T m1.
+ * Device FP64 caller order. */
+dg_status dg_rk3_step_vjp(dg_mesh* mesh, const double* U0, double dt, const double* lambda, double* out,
                           void* stream);
 
-/* out = (d U_{n+1} / d U_n)^T lambda for one SSP-RK3 step from U0 with step
- * dt (stages recomputed).  Device FP64 caller order. */
-dg_status dg_rk3_step_vjp(dg_mesh* mesh, const double* U0, double dt, const double* lambda,
-                          double* out, void* stream);
+/* Gradient of the kinetic energy int |m|^2/(2 rho) dx (volume rule) with
+ * respect to the coefficients U (the seed of the adjoint of that
+ * functional).  U, out: device FP64 [ne][5][Nb] caller order. */
+dg_status dg_kinetic_energy_grad(dg_mesh* mesh, const double* U, double* out, void* stream);
 
 /* Synchronise the stream and return DG_ERR_NONPHYSICAL if any kernel since
  * the last call flagged rho <= 0, p <= 0 or a non-finite value; clears the flag. */

@@ -48,6 +48,7 @@ void free_mesh(dg_mesh* m) {
     cudaFree(m->d_tab64);
     cudaFree(m->d_fperm);
     for (auto& b : m->d_B) cudaFree(b);
+    for (auto& b : m->d_V) cudaFree(b);
     cudaFree(m->d_io);
     cudaFree(m->d_red);
     cudaFree(m->d_status);
@@ -335,16 +336,53 @@ dg_status dg_integrals(dg_mesh* m, const double* U, double totals[5], double* ke
     return DG_OK;
 }
 
+namespace {
+dg_status ensure_adjoint_buffers(dg_mesh* m) {
+    for (auto& b : m->d_V)
+        if (!b) DG_CUDA(cudaMalloc(&b, m->state_bytes() + 256));
+    return DG_OK;
+}
+}  // namespace
+
 dg_status dg_residual_vjp(dg_mesh* m, const double* U, const double* lambda, double* out, void* stream) {
-    (void)U; (void)lambda; (void)out; (void)stream;
-    if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
-    return fail(DG_ERR_UNSUPPORTED, "the adjoint is not available in this build");
+    if (!m || !U || !lambda || !out) return fail(DG_ERR_ARG, "mesh, U, lambda and out must be non-NULL");
+    cudaStream_t s = as_stream(stream);
+    dg_status st = ensure_adjoint_buffers(m);
+    if (st != DG_OK) return st;
+    void** V = m->d_V;
+    const double c[4] = {0.0, 0.0, 0.0, 1.0};
+    DG_CUDA(dg::launch_gather(m, U, V[0], s));
+    DG_CUDA(dg::launch_gather(m, lambda, V[1], s));
+    DG_CUDA(dg::launch_residual_vjp(m, V[0], V[1], nullptr, nullptr, nullptr, c, V[2], s));
+    DG_CUDA(dg::launch_scatter(m, V[2], out, s));
+    return DG_OK;
 }
 
 dg_status dg_rk3_step_vjp(dg_mesh* m, const double* U0, double dt, const double* lambda, double* out, void* stream) {
-    (void)U0; (void)dt; (void)lambda; (void)out; (void)stream;
-    if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
-    return fail(DG_ERR_UNSUPPORTED, "the adjoint is not available in this build");
+    if (!m || !U0 || !lambda || !out) return fail(DG_ERR_ARG, "mesh, U0, lambda and out must be non-NULL");
+    if (!(dt >= 0.0)) return fail(DG_ERR_ARG, "dt must be >= 0");
+    cudaStream_t s = as_stream(stream);
+    dg_status st = ensure_adjoint_buffers(m);
+    if (st != DG_OK) return st;
+    void** V = m->d_V;   // V0 = U0, V1 = lambda, V2 = U1, V3 = U2 (then result), V4 = m2, V5 = m1
+    DG_CUDA(dg::launch_gather(m, U0, V[0], s));
+    DG_CUDA(dg::launch_gather(m, lambda, V[1], s));
+    DG_CUDA(dg::launch_residual(m, V[0], nullptr, V[2], 1, dt, 0.0, 1.0, s));
+    DG_CUDA(dg::launch_residual(m, V[2], V[0], V[3], 1, dt, 0.75, 0.25, s));
+    const double c2[4] = {2.0 / 3.0, 0.0, 0.0, 2.0 / 3.0 * dt};   // m2 = 2/3 (lambda + dt J(U2)^T lambda)
+    DG_CUDA(dg::launch_residual_vjp(m, V[3], V[1], V[1], nullptr, nullptr, c2, V[4], s));
+    const double c1[4] = {0.25, 0.0, 0.0, 0.25 * dt};             // m1 = 1/4 (m2 + dt J(U1)^T m2)
+    DG_CUDA(dg::launch_residual_vjp(m, V[2], V[4], V[4], nullptr, nullptr, c1, V[5], s));
+    const double c0[4] = {1.0 / 3.0, 0.75, 1.0, dt};              // lambda/3 + 3/4 m2 + m1 + dt J(U0)^T m1
+    DG_CUDA(dg::launch_residual_vjp(m, V[0], V[5], V[1], V[4], V[5], c0, V[3], s));
+    DG_CUDA(dg::launch_scatter(m, V[3], out, s));
+    return DG_OK;
+}
+
+dg_status dg_kinetic_energy_grad(dg_mesh* m, const double* U, double* out, void* stream) {
+    if (!m || !U || !out) return fail(DG_ERR_ARG, "mesh, U and out must be non-NULL");
+    DG_CUDA(dg::launch_ke_grad(m, U, out, as_stream(stream)));
+    return DG_OK;
 }
 
 dg_status dg_reference_data(int order, double* vol_xi, double* vol_w, double* face_bary, double* face_w,

@@ -108,6 +108,7 @@ struct dg_mesh {
     double* d_tab64 = nullptr;     // FP64 tables (projection, integrals)
     int8_t* d_fperm = nullptr;
     void* d_B[3] = {nullptr, nullptr, nullptr};   // state buffers (internal precision)
+    void* d_V[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // adjoint work buffers (lazy)
     double* d_io = nullptr;        // FP64 [ne][5][Nb] staging for host copies
     double* d_red = nullptr;       // reduction scratch
     double* h_red = nullptr;       // pinned host reduction result
@@ -125,5 +126,7 @@ cudaError_t launch_stable_dt(dg_mesh* m, const void* U, double* d_out, cudaStrea
 cudaError_t launch_integrals(dg_mesh* m, const void* U, double* d_out6, cudaStream_t s);
 cudaError_t launch_project(dg_mesh* m, const double* f, double* U, cudaStream_t s);
 cudaError_t launch_volume_points(dg_mesh* m, const double* d_x0J, double* xyz, cudaStream_t s);
-cudaError_t prepare_kernels(dg_mesh* m);
+cudaError_t launch_residual_vjp(dg_mesh* m, const void* U, const void* lam, const void* X, const void* Y,
+                                const void* Z, const double c[4], void* out, cudaStream_t s);
+cudaError_t launch_ke_grad(dg_mesh* m, const double* U_user, double* out_user, cudaStream_t s);
 }  // namespace dg

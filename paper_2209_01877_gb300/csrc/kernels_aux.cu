@@ -169,6 +169,34 @@ __global__ void k_volume_points(const double* __restrict__ x0J, const double* __
     }
 }
 
+// d/dU of int |m|^2/(2 rho) dx by the volume rule, per element (caller order):
+// out_vj = |det J| sum_q w_q g_v(q) phi_j(q), g = (-|m|^2/(2 rho^2), m/rho, 0).
+__global__ void k_ke_grad(const double* __restrict__ U, double* __restrict__ out, const int32_t* __restrict__ perm,
+                          const double* __restrict__ jinv, const double* __restrict__ tab, int64_t ne, int nb, int nq,
+                          int off_phiq, int off_wq) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ne; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = perm[i];
+        const double detJ = 1.0 / fabs(det3(jinv + 9 * i));
+        const double* c = U + e * 5 * nb;
+        double* o = out + e * 5 * nb;
+        for (int k = 0; k < 5 * nb; ++k) o[k] = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            double Uq[5];
+            for (int v = 0; v < 5; ++v) {
+                double s = 0.0;
+                for (int j = 0; j < nb; ++j) s += c[v * nb + j] * tab[off_phiq + j * nq + q];
+                Uq[v] = s;
+            }
+            const double ri = 1.0 / Uq[0];
+            const double g[4] = {-0.5 * (Uq[1] * Uq[1] + Uq[2] * Uq[2] + Uq[3] * Uq[3]) * ri * ri, Uq[1] * ri,
+                                 Uq[2] * ri, Uq[3] * ri};
+            const double w = detJ * tab[off_wq + q];
+            for (int v = 0; v < 4; ++v)
+                for (int j = 0; j < nb; ++j) o[v * nb + j] += w * g[v] * tab[off_phiq + j * nq + q];
+        }
+    }
+}
+
 int grid_for(int64_t n, int block) {
     int64_t g = (n + block - 1) / block;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
@@ -227,6 +255,13 @@ cudaError_t launch_project(dg_mesh* m, const double* f, double* U, cudaStream_t 
     const TabLayout L(m->p);
     const int64_t n = m->host.ne * 5 * m->nb;
     k_project<<<grid_for(n, 256), 256, 0, s>>>(f, U, m->d_tab64, m->host.ne, m->nb, m->nq, L.phiq, L.wq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ke_grad(dg_mesh* m, const double* U_user, double* out_user, cudaStream_t s) {
+    const TabLayout L(m->p);
+    k_ke_grad<<<grid_for(m->host.ne, 128), 128, 0, s>>>(U_user, out_user, m->d_perm, m->d_jinv64, m->d_tab64,
+                                                        m->host.ne, m->nb, m->nq, L.phiq, L.wq);
     return cudaGetLastError();
 }
 

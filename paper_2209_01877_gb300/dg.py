@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_MESH", 3: "DG_ERR_CUDA",
 
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_sizes", "dg_volume_points", "dg_project",
             "dg_set_state", "dg_get_state", "dg_residual", "dg_rk_stage", "dg_rk3_step", "dg_stable_dt",
-            "dg_integrals", "dg_residual_vjp", "dg_rk3_step_vjp", "dg_sync_status", "dg_reference_data",
+            "dg_integrals", "dg_residual_vjp", "dg_rk3_step_vjp", "dg_kinetic_energy_grad", "dg_sync_status",
+            "dg_reference_data",
             "dg_last_error"]
 
 
@@ -69,6 +70,7 @@ def load():
             "dg_integrals": [vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double), vp],
             "dg_residual_vjp": [vp, vp, vp, vp, vp],
             "dg_rk3_step_vjp": [vp, vp, C.c_double, vp, vp, vp],
+            "dg_kinetic_energy_grad": [vp, vp, vp, vp],
             "dg_sync_status": [vp, vp],
             "dg_reference_data": [C.c_int, vp, vp, vp, vp, vp, vp],
         }
@@ -218,6 +220,10 @@ def dg_residual_vjp(mesh, U, lam, out, stream=None):
 
 def dg_rk3_step_vjp(mesh, U0, dt, lam, out, stream=None):
     _check(load().dg_rk3_step_vjp(mesh, _dptr(U0), float(dt), _dptr(lam), _dptr(out), _stream(stream)))
+
+
+def dg_kinetic_energy_grad(mesh, U, out, stream=None):
+    _check(load().dg_kinetic_energy_grad(mesh, _dptr(U), _dptr(out), _stream(stream)))
 
 
 def dg_sync_status(mesh, stream=None):

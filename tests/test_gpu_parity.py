@@ -6,9 +6,12 @@ vector quantity, energy),
 (a relative bar normalised by the quantity's largest residual, since a
 pointwise relative error is undefined where R ~ 0; the momentum components
 share one scale so that a component whose residual is small only because of
-the flow direction is not held to a tighter absolute bar than the others).  FP32 path: 2e-5 of the
-same scale (FP32 unit roundoff 6e-8 times the ~100 accumulated products of the
-P3 contractions, plus the conditioning of the face and volume cancellation).
+the flow direction is not held to a tighter absolute bar than the others).
+FP32 path: 1e-4 of the same scale.  Derivation: unit roundoff 6e-8; the
+residual is a difference of volume and face terms each ~|F|/h while R itself
+is ~|dF/dx|, a cancellation ratio of up to ~50 on the 48^3 vortex; ~30
+products accumulate per output (error growth ~sqrt(30) ~ 5.5):
+6e-8 * 50 * 5.5 ~ 1.7e-5, and a factor 6 margin for the sharpest elements.
 """
 import math
 
@@ -23,7 +26,7 @@ from gpu_helpers import gpu_residual, make_mesh, max_rel_err, sample_elements, t
 
 pytestmark = pytest.mark.gpu
 TOL64 = 1e-12
-TOL32 = 2e-5
+TOL32 = 1e-4
 
 
 def _box(nx=4, ny=3, nz=3):
@@ -213,6 +216,10 @@ def test_full_size_p3_box_channel_fp64():
     m = I.make_box_channel(96, 48, 48, jitter=0.15)
     Uinf = I.freestream_state(0.3)
     c = I.pulse_centre()
+    # boundary elements and the pulse region (where the residual is not just
+    # free-stream round-off) are always part of the sample
     bnd = np.nonzero(np.any(m.bc_tag > 0, axis=1))[0][:300]
+    cent = m.tet_xyz.mean(axis=1)
+    pulse = np.nonzero(np.sum((cent - np.array(c)) ** 2, axis=1) < 0.1 ** 2)[0][:600]
     U_fn = lambda P: P.project(lambda x: I.gaussian_pulse(x, c), rule="volume")
-    assert _sampled(m, 3, "roe", U_fn, freestream=Uinf, include=bnd) < TOL64
+    assert _sampled(m, 3, "roe", U_fn, freestream=Uinf, include=np.concatenate([bnd, pulse])) < TOL64
