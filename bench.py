@@ -163,7 +163,8 @@ def run_ours(args, rank, world, device):
 
     mesh, field, w = make_workload(args.workload)
     p, flux = w["p"], w["flux"]
-    precision = {"auto": dg.DG_FP64, "fp64": dg.DG_FP64, "fp32": dg.DG_FP32}[args.precision]
+    precision = {"auto": dg.DG_MIXED_FP16, "mixed": dg.DG_MIXED_FP16, "fp64": dg.DG_FP64,
+                 "fp32": dg.DG_FP32}[args.precision]
     fs = (0, 0, 0, 0, 0)
     if w["box"]:
         from paper_2209_01877_gb300 import inputs as I
@@ -224,7 +225,7 @@ def run_ours(args, rank, world, device):
     value = world * 3 * dofs * args.steps / t_total
 
     # roofline of the dominant kernel (the fused residual + RK-stage kernel)
-    s_state = 8 if precision == dg.DG_FP64 else 4
+    s_state = 4 if precision == dg.DG_FP32 else 8     # FP64, or the float-float pair of the mixed form
     peaks, peak_src = measured_peaks()
     tot_bytes = tot_flops = tot_ms = 0.0
     for st in (1, 2, 3):
@@ -247,9 +248,10 @@ def run_ours(args, rank, world, device):
                 "kernel": "k_residual<double,P,FLUX,RK>", "algorithmic_bytes_per_launch": bytes_per_launch,
                 "algorithmic_flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms}
     else:
+        kname = "k_residual<float,P,FLUX,RK>" if precision == dg.DG_FP32 else "k_residual_mixed<P,FLUX>"
         roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": hbm_achieved / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": f"hbm_gbs of {peak_src} peaks", "kernel": "k_residual<float,P,FLUX,RK>",
+                "peak_source": f"hbm_gbs of {peak_src} peaks", "kernel": kname,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms}
 
     # end to end through the C ABI with pinned host buffers
@@ -272,8 +274,9 @@ def run_ours(args, rank, world, device):
         e2e = {"value": world * 3 * dofs * nrep / te, "unit": "DOF-updates/s", "h2d_bytes_per_step": dofs * 8,
                "d2h_bytes_per_step": dofs * 8, "steps": nrep}
     M.close()
+    pname = {dg.DG_FP64: "f64", dg.DG_FP32: "f32", dg.DG_MIXED_FP16: "f16x2-tc/f32/ff32"}[precision]
     return dict(value=value, ms_per_step=ms_per_step, roofline=roof, clocks=clk, e2e=e2e, t_local=t_local,
-                precision="f64" if precision == dg.DG_FP64 else "f32", ne=ne, p=p, flux=flux,
+                precision=pname, ne=ne, p=p, flux=flux,
                 stage_ms=[float(np.mean(x)) for x in stage_ms], nlaunch=nlaunch)
 
 
@@ -371,7 +374,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64", "fp32"])
+    ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 comparison leg of a mixed run")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -398,13 +402,22 @@ def main():
         except Exception as e:  # reported, not fatal
             cpu_base = {"value": None, "error": str(e)[-300:]}
     r = run_ours(args, rank, world, device)
+    fp64_leg = None
+    if r["precision"].startswith("f16") and not args.no_fp64_leg:
+        import copy
+        a64 = copy.copy(args)
+        a64.precision, a64.steps, a64.no_e2e = "fp64", 2, True
+        r64 = run_ours(a64, rank, world, device)
+        fp64_leg = {"value": r64["value"], "unit": "DOF-updates/s", "ms_per_step": r64["ms_per_step"], "steps": 2,
+                    "warmup": a64.warmup, "roofline": r64["roofline"],
+                    "mixed_over_fp64": r["value"] / r64["value"]}
     if rank == 0:
         line = {"metric": METRIC, "value": r["value"], "unit": "DOF-updates/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": r["precision"],
                 "data": "synthetic", "config": config_of(args), "roofline": r["roofline"],
                 "cpu_baseline": cpu_base, "e2e": r["e2e"], "clocks": r["clocks"],
-                "gpu_launches": r["nlaunch"], "stage_ms": r["stage_ms"]}
+                "gpu_launches": r["nlaunch"], "stage_ms": r["stage_ms"], "fp64": fp64_leg}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

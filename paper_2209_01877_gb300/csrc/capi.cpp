@@ -28,7 +28,9 @@ dg_status cuda_fail(cudaError_t e, const char* where) {
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
-size_t real_size(int precision) { return precision == DG_FP64 ? sizeof(double) : sizeof(float); }
+// bytes per stored coefficient: FP64, FP32, or a float-float pair (mixed precision)
+size_t real_size(int precision) { return precision == DG_FP32 ? sizeof(float) : 8; }
+bool is_mixed(const dg_mesh* m) { return m->precision == DG_MIXED_FP16; }
 
 template <typename T>
 dg_status upload(T** dst, const T* src, size_t n, cudaStream_t s) {
@@ -47,6 +49,7 @@ void free_mesh(dg_mesh* m) {
     cudaFree(m->d_tab);
     cudaFree(m->d_tab64);
     cudaFree(m->d_fperm);
+    cudaFree(m->d_tab16);
     for (auto& b : m->d_B) cudaFree(b);
     for (auto& b : m->d_V) cudaFree(b);
     cudaFree(m->d_io);
@@ -75,8 +78,8 @@ dg_status dg_mesh_create(const int32_t* tet_vid, const double* tet_xyz, const in
     if (ne <= 0 || ne > (int64_t)INT32_MAX / 4) return fail(DG_ERR_ARG, "ne out of range");
     if (cfg->order < 1 || cfg->order > 3) return fail(DG_ERR_ARG, "order must be 1, 2 or 3");
     if (cfg->precision < DG_FP64 || cfg->precision > DG_MIXED_BF16) return fail(DG_ERR_ARG, "bad precision");
-    if (cfg->precision == DG_MIXED_FP16 || cfg->precision == DG_MIXED_BF16)
-        return fail(DG_ERR_UNSUPPORTED, "mixed precision is not available in this build");
+    if (cfg->precision == DG_MIXED_BF16)
+        return fail(DG_ERR_UNSUPPORTED, "the BF16 mixed form is not available in this build (use DG_MIXED_FP16)");
     if (cfg->flux != DG_RUSANOV && cfg->flux != DG_ROE) return fail(DG_ERR_ARG, "bad flux");
     if (!(cfg->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must exceed 1");
     if (cfg->renumber < DG_ORDER_ASIS || cfg->renumber > DG_ORDER_MORTON) return fail(DG_ERR_ARG, "bad renumber");
@@ -135,6 +138,11 @@ dg_status dg_mesh_create(const int32_t* tet_vid, const double* tet_xyz, const in
     DG_TRY(upload(&m->d_tab64, tab64.data(), tab64.size(), s));
     std::vector<float> tab32(m->ref.tab.begin(), m->ref.tab.end());
     std::vector<float> jinv32(m->host.jinv.begin(), m->host.jinv.end());
+    if (m->precision == DG_MIXED_FP16) {
+        std::vector<uint16_t> t16;
+        dg::build_mixed_tables(m->p, m->ref, t16, m->mix_inv_b1, m->mix_inv_b2);
+        DG_TRY(upload(&m->d_tab16, t16.data(), t16.size(), s));
+    }
     if (m->precision == DG_FP64) {
         m->d_tab = m->d_tab64;   // shared; freed once below
         m->d_jinv = m->d_jinv64;
@@ -273,10 +281,29 @@ dg_status dg_residual(dg_mesh* m, const double* U, double* R, void* stream) {
     } else if (!m->has_state) {
         return fail(DG_ERR_NOSTATE, "no state set and U is NULL");
     }
+    if (is_mixed(m)) {
+        const float* hi = static_cast<const float*>(in);
+        float* out = static_cast<float*>(m->d_B[2]);
+        DG_CUDA(dg::launch_residual_mixed(m, hi, nullptr, nullptr, nullptr, out, nullptr, 0, 0.0, 0.0, 0.0, s));
+        DG_CUDA(dg::launch_scatter_f32(m, out, R, s));
+        return DG_OK;
+    }
     DG_CUDA(dg::launch_residual(m, in, nullptr, m->d_B[2], 0, 0.0, 0.0, 0.0, s));
     DG_CUDA(dg::launch_scatter(m, m->d_B[2], R, s));
     return DG_OK;
 }
+
+namespace {
+// one fused residual + RK stage: out = a U0 + b (U + dt R(U))
+cudaError_t stage_launch(dg_mesh* m, void* U, void* U0, void* out, double dt, double a, double b, cudaStream_t s) {
+    if (!is_mixed(m)) return dg::launch_residual(m, U, U0, out, 1, dt, a, b, s);
+    const size_t n = (size_t)m->host.ne * 5 * m->nb;
+    float* u = static_cast<float*>(U);
+    float* u0 = static_cast<float*>(U0);
+    float* o = static_cast<float*>(out);
+    return dg::launch_residual_mixed(m, u, u + n, u0, u0 ? u0 + n : nullptr, o, o + n, 1, dt, a, b, s);
+}
+}  // namespace
 
 dg_status dg_rk_stage(dg_mesh* m, int stage, double dt, void* stream) {
     if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
@@ -285,9 +312,9 @@ dg_status dg_rk_stage(dg_mesh* m, int stage, double dt, void* stream) {
     cudaStream_t s = as_stream(stream);
     void** B = m->d_B;
     switch (stage) {
-        case 1: DG_CUDA(dg::launch_residual(m, B[0], nullptr, B[1], 1, dt, 0.0, 1.0, s)); break;
-        case 2: DG_CUDA(dg::launch_residual(m, B[1], B[0], B[2], 1, dt, 0.75, 0.25, s)); break;
-        case 3: DG_CUDA(dg::launch_residual(m, B[2], B[0], B[0], 1, dt, 1.0 / 3.0, 2.0 / 3.0, s)); break;
+        case 1: DG_CUDA(stage_launch(m, B[0], nullptr, B[1], dt, 0.0, 1.0, s)); break;
+        case 2: DG_CUDA(stage_launch(m, B[1], B[0], B[2], dt, 0.75, 0.25, s)); break;
+        case 3: DG_CUDA(stage_launch(m, B[2], B[0], B[0], dt, 1.0 / 3.0, 2.0 / 3.0, s)); break;
         default: return fail(DG_ERR_ARG, "stage must be 1, 2 or 3");
     }
     return DG_OK;
@@ -346,6 +373,7 @@ dg_status ensure_adjoint_buffers(dg_mesh* m) {
 
 dg_status dg_residual_vjp(dg_mesh* m, const double* U, const double* lambda, double* out, void* stream) {
     if (!m || !U || !lambda || !out) return fail(DG_ERR_ARG, "mesh, U, lambda and out must be non-NULL");
+    if (is_mixed(m)) return fail(DG_ERR_UNSUPPORTED, "the adjoint runs in FP64 or FP32 meshes");
     cudaStream_t s = as_stream(stream);
     dg_status st = ensure_adjoint_buffers(m);
     if (st != DG_OK) return st;
@@ -360,6 +388,7 @@ dg_status dg_residual_vjp(dg_mesh* m, const double* U, const double* lambda, dou
 
 dg_status dg_rk3_step_vjp(dg_mesh* m, const double* U0, double dt, const double* lambda, double* out, void* stream) {
     if (!m || !U0 || !lambda || !out) return fail(DG_ERR_ARG, "mesh, U0, lambda and out must be non-NULL");
+    if (is_mixed(m)) return fail(DG_ERR_UNSUPPORTED, "the adjoint runs in FP64 or FP32 meshes");
     if (!(dt >= 0.0)) return fail(DG_ERR_ARG, "dt must be >= 0");
     cudaStream_t s = as_stream(stream);
     dg_status st = ensure_adjoint_buffers(m);
@@ -412,6 +441,7 @@ dg_status dg_sync_status(dg_mesh* m, void* stream) {
     DG_CUDA(cudaStreamSynchronize(s));
     DG_CUDA(cudaMemsetAsync(m->d_status, 0, sizeof(unsigned int), s));
     DG_CUDA(cudaStreamSynchronize(s));
+    if (flag & 2u) return fail(DG_ERR_TIMEOUT, "a bounded tensor-core completion wait gave up");
     if (flag & 1u) return fail(DG_ERR_NONPHYSICAL, "non-positive density or pressure (or non-finite value) seen on the device");
     return DG_OK;
 }

@@ -107,6 +107,8 @@ struct dg_mesh {
     void* d_tab = nullptr;         // Real tables
     double* d_tab64 = nullptr;     // FP64 tables (projection, integrals)
     int8_t* d_fperm = nullptr;
+    uint16_t* d_tab16 = nullptr;   // f16 operand images of the tables (mixed precision)
+    float mix_inv_b1 = 1.f, mix_inv_b2 = 1.f;
     void* d_B[3] = {nullptr, nullptr, nullptr};   // state buffers (internal precision)
     void* d_V[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // adjoint work buffers (lazy)
     double* d_io = nullptr;        // FP64 [ne][5][Nb] staging for host copies
@@ -122,6 +124,7 @@ cudaError_t launch_residual(dg_mesh* m, const void* U, const void* U0, void* out
                             double dt, double a, double b, cudaStream_t s);
 cudaError_t launch_gather(dg_mesh* m, const double* user, void* internal, cudaStream_t s);   // caller -> internal
 cudaError_t launch_scatter(dg_mesh* m, const void* internal, double* user, cudaStream_t s);  // internal -> caller
+cudaError_t launch_scatter_f32(dg_mesh* m, const float* internal, double* user, cudaStream_t s);
 cudaError_t launch_stable_dt(dg_mesh* m, const void* U, double* d_out, cudaStream_t s);
 cudaError_t launch_integrals(dg_mesh* m, const void* U, double* d_out6, cudaStream_t s);
 cudaError_t launch_project(dg_mesh* m, const double* f, double* U, cudaStream_t s);
@@ -129,4 +132,10 @@ cudaError_t launch_volume_points(dg_mesh* m, const double* d_x0J, double* xyz, c
 cudaError_t launch_residual_vjp(dg_mesh* m, const void* U, const void* lam, const void* X, const void* Y,
                                 const void* Z, const double c[4], void* out, cudaStream_t s);
 cudaError_t launch_ke_grad(dg_mesh* m, const double* U_user, double* out_user, cudaStream_t s);
+// mixed precision (tensor cores): state stored as float-float planes (hi, then lo)
+cudaError_t launch_residual_mixed(dg_mesh* m, const float* U_hi, const float* U_lo, const float* U0_hi,
+                                  const float* U0_lo, float* out_hi, float* out_lo, int mode, double dt, double a,
+                                  double b, cudaStream_t s);
+void build_mixed_tables(int p, const RefData& ref, std::vector<uint16_t>& out, float& inv_b1, float& inv_b2);
+int mixed_tab_halves(int p);
 }  // namespace dg

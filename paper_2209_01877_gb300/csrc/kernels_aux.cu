@@ -24,6 +24,28 @@ __global__ void k_gather(const double* __restrict__ user, Real* __restrict__ int
     }
 }
 
+// caller FP64 -> internal float-float planes (hi = fl32(x), lo = fl32(x - hi))
+__global__ void k_gather_ff(const double* __restrict__ user, float* __restrict__ hi, float* __restrict__ lo,
+                            const int32_t* __restrict__ perm, int64_t ne, int nv) {
+    const int64_t n = ne * nv;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = i / nv, k = i - e * nv;
+        const double x = user[(int64_t)perm[e] * nv + k];
+        const float h = (float)x;
+        hi[i] = h;
+        lo[i] = (float)(x - (double)h);
+    }
+}
+
+__global__ void k_scatter_ff(const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ user,
+                             const int32_t* __restrict__ perm, int64_t ne, int nv) {
+    const int64_t n = ne * nv;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = i / nv, k = i - e * nv;
+        user[(int64_t)perm[e] * nv + k] = (double)hi[i] + (double)lo[i];
+    }
+}
+
 template <typename Real>
 __global__ void k_scatter(const Real* __restrict__ internal, double* __restrict__ user, const int32_t* __restrict__ perm,
                           int64_t ne, int nv) {
@@ -58,14 +80,16 @@ __device__ __forceinline__ double det3(const double* I) {
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(RT) k_dt_local(const Real* __restrict__ U, const double* __restrict__ jinv, int64_t ne,
+__global__ void __launch_bounds__(RT) k_dt_local(const Real* __restrict__ U, const Real* __restrict__ Ulo,
+                                                 const double* __restrict__ jinv, int64_t ne,
                                                  int nb, int p, double gamma, double* __restrict__ block_min,
                                                  unsigned int* status) {
     __shared__ double red[RT];
     double best = INFINITY;
     for (int64_t e = blockIdx.x * (int64_t)RT + threadIdx.x; e < ne; e += (int64_t)gridDim.x * RT) {
         double m[5];
-        for (int v = 0; v < 5; ++v) m[v] = SQRT6 * (double)U[(e * 5 + v) * nb];   // element means
+        for (int v = 0; v < 5; ++v)   // element means
+            m[v] = SQRT6 * ((double)U[(e * 5 + v) * nb] + (Ulo ? (double)Ulo[(e * 5 + v) * nb] : 0.0));
         const double rho = m[0];
         const double u2 = (m[1] * m[1] + m[2] * m[2] + m[3] * m[3]) / (rho * rho);
         const double pr = (gamma - 1.0) * (m[4] - 0.5 * rho * u2);
@@ -98,7 +122,8 @@ __global__ void __launch_bounds__(RT) k_min_final(const double* __restrict__ in,
 
 // Per element: |det J| * (int_T U_v = c_v0 / sqrt6) and |det J| * sum_q w_q |m|^2/(2 rho).
 template <typename Real>
-__global__ void __launch_bounds__(RT) k_integrals_local(const Real* __restrict__ U, const double* __restrict__ jinv,
+__global__ void __launch_bounds__(RT) k_integrals_local(const Real* __restrict__ U, const Real* __restrict__ Ulo,
+                                                        const double* __restrict__ jinv,
                                                         const double* __restrict__ tab, int64_t ne, int nb, int nq,
                                                         int off_phiq, int off_wq, double* __restrict__ block_sum) {
     __shared__ double red[6][RT];
@@ -106,13 +131,15 @@ __global__ void __launch_bounds__(RT) k_integrals_local(const Real* __restrict__
     for (int64_t e = blockIdx.x * (int64_t)RT + threadIdx.x; e < ne; e += (int64_t)gridDim.x * RT) {
         const double detJ = 1.0 / fabs(det3(jinv + 9 * e));
         const Real* c = U + e * 5 * nb;
-        for (int v = 0; v < 5; ++v) acc[v] += detJ * (double)c[v * nb] / SQRT6;
+        const Real* cl = Ulo ? Ulo + e * 5 * nb : nullptr;
+        for (int v = 0; v < 5; ++v) acc[v] += detJ * ((double)c[v * nb] + (cl ? (double)cl[v * nb] : 0.0)) / SQRT6;
         double ke = 0.0;
         for (int q = 0; q < nq; ++q) {
             double Uq[5];
             for (int v = 0; v < 5; ++v) {
                 double s = 0.0;
-                for (int j = 0; j < nb; ++j) s += (double)c[v * nb + j] * tab[off_phiq + j * nq + q];
+                for (int j = 0; j < nb; ++j)
+                    s += ((double)c[v * nb + j] + (cl ? (double)cl[v * nb + j] : 0.0)) * tab[off_phiq + j * nq + q];
                 Uq[v] = s;
             }
             ke += tab[off_wq + q] * 0.5 * (Uq[1] * Uq[1] + Uq[2] * Uq[2] + Uq[3] * Uq[3]) / Uq[0];
@@ -209,8 +236,11 @@ cudaError_t launch_gather(dg_mesh* m, const double* user, void* internal, cudaSt
     const int64_t n = m->host.ne * nv;
     if (m->precision == DG_FP64)
         k_gather<double><<<grid_for(n, 256), 256, 0, s>>>(user, static_cast<double*>(internal), m->d_perm, m->host.ne, nv);
-    else
+    else if (m->precision == DG_FP32)
         k_gather<float><<<grid_for(n, 256), 256, 0, s>>>(user, static_cast<float*>(internal), m->d_perm, m->host.ne, nv);
+    else
+        k_gather_ff<<<grid_for(n, 256), 256, 0, s>>>(user, static_cast<float*>(internal),
+                                                     static_cast<float*>(internal) + n, m->d_perm, m->host.ne, nv);
     return cudaGetLastError();
 }
 
@@ -219,8 +249,19 @@ cudaError_t launch_scatter(dg_mesh* m, const void* internal, double* user, cudaS
     const int64_t n = m->host.ne * nv;
     if (m->precision == DG_FP64)
         k_scatter<double><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const double*>(internal), user, m->d_perm, m->host.ne, nv);
-    else
+    else if (m->precision == DG_FP32)
         k_scatter<float><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const float*>(internal), user, m->d_perm, m->host.ne, nv);
+    else
+        k_scatter_ff<<<grid_for(n, 256), 256, 0, s>>>(static_cast<const float*>(internal),
+                                                      static_cast<const float*>(internal) + n, user, m->d_perm,
+                                                      m->host.ne, nv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_f32(dg_mesh* m, const float* internal, double* user, cudaStream_t s) {
+    const int nv = 5 * m->nb;
+    const int64_t n = m->host.ne * nv;
+    k_scatter<float><<<grid_for(n, 256), 256, 0, s>>>(internal, user, m->d_perm, m->host.ne, nv);
     return cudaGetLastError();
 }
 
@@ -228,12 +269,14 @@ int reduction_blocks(int64_t ne) { return (int)std::max<int64_t>(1, std::min<int
 
 cudaError_t launch_stable_dt(dg_mesh* m, const void* U, double* d_out, cudaStream_t s) {
     const int nblk = reduction_blocks(m->host.ne);
+    const int64_t n = m->host.ne * 5 * m->nb;
     if (m->precision == DG_FP64)
-        k_dt_local<double><<<nblk, RT, 0, s>>>(static_cast<const double*>(U), m->d_jinv64, m->host.ne, m->nb, m->p,
-                                               m->gamma, m->d_red, m->d_status);
+        k_dt_local<double><<<nblk, RT, 0, s>>>(static_cast<const double*>(U), nullptr, m->d_jinv64, m->host.ne, m->nb,
+                                               m->p, m->gamma, m->d_red, m->d_status);
     else
-        k_dt_local<float><<<nblk, RT, 0, s>>>(static_cast<const float*>(U), m->d_jinv64, m->host.ne, m->nb, m->p,
-                                              m->gamma, m->d_red, m->d_status);
+        k_dt_local<float><<<nblk, RT, 0, s>>>(static_cast<const float*>(U),
+                                              m->precision == DG_FP32 ? nullptr : static_cast<const float*>(U) + n,
+                                              m->d_jinv64, m->host.ne, m->nb, m->p, m->gamma, m->d_red, m->d_status);
     k_min_final<<<1, RT, 0, s>>>(m->d_red, nblk, d_out);
     return cudaGetLastError();
 }
@@ -241,12 +284,15 @@ cudaError_t launch_stable_dt(dg_mesh* m, const void* U, double* d_out, cudaStrea
 cudaError_t launch_integrals(dg_mesh* m, const void* U, double* d_out6, cudaStream_t s) {
     const int nblk = reduction_blocks(m->host.ne);
     const TabLayout L(m->p);
+    const int64_t n = m->host.ne * 5 * m->nb;
     if (m->precision == DG_FP64)
-        k_integrals_local<double><<<nblk, RT, 0, s>>>(static_cast<const double*>(U), m->d_jinv64, m->d_tab64, m->host.ne,
-                                                      m->nb, m->nq, L.phiq, L.wq, m->d_red);
+        k_integrals_local<double><<<nblk, RT, 0, s>>>(static_cast<const double*>(U), nullptr, m->d_jinv64, m->d_tab64,
+                                                      m->host.ne, m->nb, m->nq, L.phiq, L.wq, m->d_red);
     else
-        k_integrals_local<float><<<nblk, RT, 0, s>>>(static_cast<const float*>(U), m->d_jinv64, m->d_tab64, m->host.ne,
-                                                     m->nb, m->nq, L.phiq, L.wq, m->d_red);
+        k_integrals_local<float><<<nblk, RT, 0, s>>>(static_cast<const float*>(U),
+                                                     m->precision == DG_FP32 ? nullptr : static_cast<const float*>(U) + n,
+                                                     m->d_jinv64, m->d_tab64, m->host.ne, m->nb, m->nq, L.phiq, L.wq,
+                                                     m->d_red);
     k_sum_final<<<1, RT, 0, s>>>(m->d_red, nblk, d_out6);
     return cudaGetLastError();
 }

@@ -31,16 +31,38 @@ def gpu_residual(M, U):
     return R.cpu().numpy()
 
 
-def max_rel_err(got, ref, axis_var=1):
+def max_rel_err(got, ref, axis_var=1, term_scale=None):
     """Largest error over the conserved quantities, each normalised by that
-    quantity's largest |ref|: mass, momentum (the three components as one
-    vector quantity, so the scale does not depend on the axes) and energy."""
+    quantity's scale: the larger of max|ref| over the quantity's entries and,
+    if given, ``term_scale[Q]`` (the magnitude of the volume / face terms whose
+    difference forms the residual, see ``residual_term_scale``).  Quantities:
+    mass, momentum (the three components as one vector quantity, so the scale
+    does not depend on the axes) and energy."""
     out = 0.0
-    for group in ((0,), (1, 2, 3), (4,)):
+    for gi, group in enumerate(((0,), (1, 2, 3), (4,))):
         r = np.take(ref, group, axis=axis_var)
         g = np.take(got, group, axis=axis_var)
-        out = max(out, float(np.abs(g - r).max() / max(np.abs(r).max(), 1e-300)))
+        scale = float(np.abs(r).max())
+        if term_scale is not None:
+            scale = max(scale, float(term_scale[gi]))
+        out = max(out, float(np.abs(g - r).max() / max(scale, 1e-300)))
     return out
+
+
+def residual_term_scale(P, U, rows=None):
+    """Per conserved quantity, max over elements of |F_Q(mean state)| * |grad lambda|_max:
+    the size of one face (or volume) term of the residual, before the terms
+    cancel.  Round-off in R is a multiple of machine epsilon times this."""
+    from oracle import euler
+    from oracle.mesh import face_normal_area
+    e = np.arange(P.ne) if rows is None else np.asarray(rows)
+    Ub = np.sqrt(6.0) * U[e, :, 0]
+    F = np.abs(euler.euler_flux(Ub, P.gamma)).max(axis=1)            # [E,5]
+    vol = P.det[e] / 6.0
+    amax = np.max(np.stack([face_normal_area(P.xyz, e, f)[1] for f in range(4)]), axis=0)
+    inv_h = amax / (3.0 * vol)
+    s = F * inv_h[:, None]
+    return [s[:, 0].max(), s[:, 1:4].max(), s[:, 4].max()]
 
 
 def sample_elements(ne, count, seed=7, include=()):

@@ -1,0 +1,128 @@
+"""GPU checks of the mixed-precision path (tensor-core split-f16 contractions,
+FP32 flux, float-float RK accumulation) against the FP64 oracle.
+
+Residual tolerance 5e-6 of max(max|R_Q|, S_Q) (the term scale of
+test_gpu_parity): each contraction operand is an f16 pair carrying ~22 bits
+(2^-22 = 2.4e-7 relative), a product of two such operands ~3 x 2.4e-7, FP32
+accumulation over <= 128 terms, flux and Riemann solver in FP32 (6e-8); the
+difference of volume and face terms at the term scale then carries ~1e-6;
+factor 5 margin.  Observed ~7e-7 on the P3 vortex (the FP32 CUDA-core path
+shows the same level).
+
+Accuracy bar of the mixed form (R19): after N SSP-RK3 steps of the isentropic
+vortex on the 64^3 x 6 P3 mesh, |e_mixed - e_fp64| <= 0.02 e_fp64, e the L2
+density error against the exact translated vortex.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.dg import Problem
+from paper_2209_01877_gb300 import dg
+from paper_2209_01877_gb300 import inputs as I
+
+from gpu_helpers import gpu_residual, max_rel_err, residual_term_scale, torch_cuda, vortex_state
+
+pytestmark = pytest.mark.gpu
+TOLMIX = 5e-6
+
+
+def _mesh(m, p, flux, precision=dg.DG_MIXED_FP16, fs=None):
+    tag = None if all(m.periodic) else m.bc_tag
+    return dg.Mesh(m.tet_vid, m.tet_xyz, tag, order=p, precision=precision,
+                   flux=dg.DG_ROE if flux == "roe" else dg.DG_RUSANOV, renumber=dg.DG_ORDER_RCM,
+                   freestream=tuple(fs) if fs is not None else (0, 0, 0, 0, 0))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("flux", ["rusanov", "roe"])
+def test_mixed_residual_periodic(p, flux):
+    m = I.make_periodic_cube(4, jitter=0.15)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=p, flux=flux)
+    U = vortex_state(P, radius=0.15)
+    R = P.residual(U)
+    Rg = gpu_residual(_mesh(m, p, flux), U)
+    assert max_rel_err(Rg, R, term_scale=residual_term_scale(P, U)) < TOLMIX
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_mixed_residual_box(p):
+    m = I.make_box_channel(4, 3, 3, lengths=(2.0, 1.0, 1.0), jitter=0.15)
+    fs = I.freestream_state(0.3)
+    P = Problem(m.tet_vid, m.tet_xyz, m.bc_tag, p=p, flux="roe", freestream=fs)
+    U = P.project(lambda x: I.gaussian_pulse(x, (0.9, 0.5, 0.5), width=0.3))
+    R = P.residual(U)
+    Rg = gpu_residual(_mesh(m, p, "roe", fs=fs), U)
+    assert max_rel_err(Rg, R, term_scale=residual_term_scale(P, U)) < TOLMIX
+
+
+def test_mixed_ragged_tile_and_free_stream():
+    """A mesh whose element count is not a multiple of the 24-element tile,
+    and free-stream preservation through the tensor-core path."""
+    m = I.make_box_mesh((3, 2, 3), periodic=(True, True, True), jitter=0.15)
+    assert m.ne % 24 != 0
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=3, flux="roe")
+    U = vortex_state(P, radius=0.2)
+    Rg = gpu_residual(_mesh(m, 3, "roe"), U)
+    assert max_rel_err(Rg, P.residual(U), term_scale=residual_term_scale(P, U)) < TOLMIX
+    Uf = P.project(I.uniform_flow)
+    Rf = gpu_residual(_mesh(m, 3, "roe"), Uf)
+    assert np.abs(Rf).max() < 1e-5 * max(residual_term_scale(P, Uf))
+
+
+def test_mixed_rk_steps_track_fp64():
+    """Float-float accumulation: 10 steps stay within 1e-6 of the oracle's FP64
+    trajectory (relative to the state), far below FP32 accumulation."""
+    m = I.make_periodic_cube(4, jitter=0.15)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=3, flux="roe")
+    U0 = vortex_state(P, radius=0.15)
+    dt = P.stable_dt(U0, 0.1)
+    ref = P.rk3(U0, dt, 10)
+    M = _mesh(m, 3, "roe")
+    dg.dg_set_state(M.handle, U0)
+    dg.dg_rk3_step(M.handle, dt, 10)
+    U = np.empty_like(U0)
+    dg.dg_get_state(M.handle, U)
+    dg.dg_sync_status(M.handle)
+    assert np.abs(U - ref).max() < 1e-6 * np.abs(ref).max()
+    # state round trip through the float-float planes is exact to ~1e-15
+    M2 = _mesh(m, 3, "roe")
+    dg.dg_set_state(M2.handle, U0)
+    back = np.empty_like(U0)
+    dg.dg_get_state(M2.handle, back)
+    assert np.abs(back - U0).max() < 1e-14 * np.abs(U0).max()
+    tot, _ = dg.dg_integrals(M2.handle)
+    np.testing.assert_allclose(tot, P.integrals(U0)[0], rtol=1e-12, atol=1e-14)
+
+
+def _vortex_error(P, U, t):
+    return P.l2_error(U, lambda x: I.isentropic_vortex(x, t=t), nquad=P.p + 2)
+
+
+@pytest.mark.slow
+def test_mixed_vortex_accuracy_within_2pct_of_fp64():
+    """64^3 x 6 P3 vortex (Roe), 200 SSP-RK3 steps at CFL 0.1: the L2 density
+    error of the mixed form is within 2% of the FP64 discretisation error."""
+    m = I.make_periodic_cube(64, jitter=0.15)
+    nsteps = 200
+    errs = {}
+    for prec in (dg.DG_FP64, dg.DG_MIXED_FP16):
+        M = _mesh(m, 3, "roe", precision=prec)
+        U0 = M.project(lambda x: I.isentropic_vortex(x))
+        dg.dg_set_state(M.handle, U0)
+        dt = dg.dg_stable_dt(M.handle, 0.1)
+        dg.dg_rk3_step(M.handle, dt, nsteps)
+        U = np.empty_like(U0)
+        dg.dg_get_state(M.handle, U)
+        dg.dg_sync_status(M.handle)
+        errs[prec] = (U, dt)
+        M.close()
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=3, flux="roe")
+    t = nsteps * errs[dg.DG_FP64][1]
+    e64 = _vortex_error(P, errs[dg.DG_FP64][0], t)
+    emx = _vortex_error(P, errs[dg.DG_MIXED_FP16][0], t)
+    diff = float(np.sqrt(np.mean((errs[dg.DG_FP64][0] - errs[dg.DG_MIXED_FP16][0]) ** 2)))
+    print(f"vortex L2 density error: fp64 {e64:.4e} mixed {emx:.4e} rel diff {abs(emx - e64) / e64:.2e}, "
+          f"rms coefficient difference {diff:.2e}")
+    assert abs(emx - e64) <= 0.02 * e64

@@ -2,11 +2,16 @@
 
 Tolerance (FP64 path): per conserved quantity Q (mass, momentum as one
 vector quantity, energy),
-  max |R_gpu - R_oracle| <= 1e-12 * max |R_oracle[Q]|
-(a relative bar normalised by the quantity's largest residual, since a
+  max |R_gpu - R_oracle| <= 1e-12 * max(max |R_oracle[Q]|, S_Q)
+a relative bar: normalised by the quantity's largest residual, since a
 pointwise relative error is undefined where R ~ 0; the momentum components
 share one scale so that a component whose residual is small only because of
-the flow direction is not held to a tighter absolute bar than the others).
+the flow direction is not held to a tighter absolute bar than the others; and
+never below 1e-12 of S_Q, the size of the individual volume/face terms
+(|F_Q| / h) whose difference forms R -- in free-stream regions R is pure
+cancellation round-off of order eps * S_Q in both implementations (observed:
+7e-13 absolute on the 96x48x48 channel, where the pulse's energy residual is
+only 0.015).
 FP32 path: 1e-4 of the same scale.  Derivation: unit roundoff 6e-8; the
 residual is a difference of volume and face terms each ~|F|/h while R itself
 is ~|dF/dx|, a cancellation ratio of up to ~50 on the 48^3 vortex; ~30
@@ -22,7 +27,8 @@ from oracle.dg import Problem
 from paper_2209_01877_gb300 import dg
 from paper_2209_01877_gb300 import inputs as I
 
-from gpu_helpers import gpu_residual, make_mesh, max_rel_err, sample_elements, torch_cuda, vortex_state
+from gpu_helpers import (gpu_residual, make_mesh, max_rel_err, residual_term_scale, sample_elements, torch_cuda,
+                         vortex_state)
 
 pytestmark = pytest.mark.gpu
 TOL64 = 1e-12
@@ -51,7 +57,7 @@ def test_residual_periodic_fp64(p, flux):
     U = vortex_state(P, radius=0.15)
     R = P.residual(U)
     M = make_mesh(m, p, flux)
-    assert max_rel_err(gpu_residual(M, U), R) < TOL64
+    assert max_rel_err(gpu_residual(M, U), R, term_scale=residual_term_scale(P, U)) < TOL64
 
 
 @pytest.mark.parametrize("p", [1, 2, 3])
@@ -64,7 +70,7 @@ def test_residual_box_boundaries_fp64(p, flux):
     R = P.residual(U)
     M = make_mesh(m, p, flux, freestream=Uinf)
     assert M.info()["n_bfaces"] == 4 * (3 * 3 + 4 * 3 + 4 * 3)
-    assert max_rel_err(gpu_residual(M, U), R) < TOL64
+    assert max_rel_err(gpu_residual(M, U), R, term_scale=residual_term_scale(P, U)) < TOL64
 
 
 @pytest.mark.parametrize("p", [1, 3])
@@ -74,7 +80,7 @@ def test_residual_fp32(p):
     U = vortex_state(P, radius=0.15)
     R = P.residual(U)
     M = make_mesh(m, p, "roe", precision="fp32")
-    assert max_rel_err(gpu_residual(M, U), R) < TOL32
+    assert max_rel_err(gpu_residual(M, U), R, term_scale=residual_term_scale(P, U)) < TOL32
 
 
 def test_renumbering_is_a_permutation():
@@ -194,7 +200,7 @@ def _sampled(m, p, flux, U_fn, freestream=None, nsample=1500, precision="fp64", 
     R = gpu_residual(M, U)
     rows = sample_elements(m.ne, nsample, include=include)
     ref = P.residual(U, rows)
-    return max_rel_err(R[rows], ref)
+    return max_rel_err(R[rows], ref, term_scale=residual_term_scale(P, U, rows))
 
 
 @pytest.mark.slow
