@@ -169,6 +169,28 @@ dg_status dg_sync_status(dg_mesh* mesh, void* stream);
 dg_status dg_reference_data(int order, double* vol_xi, double* vol_w, double* face_bary, double* face_w,
                             double* phi, double* dphi);
 
+/* Totals int U_v dx of the 5 conserved variables, for callers that cannot
+ * allocate device memory: code being captured into a CUDA graph, a host that
+ * gives the library a fixed memory arena and forbids further allocation, or a
+ * real-time loop that must stay off the allocator.  The paper has no
+ * counterpart; it computes what dg_integrals reports as totals, without a
+ * mesh object.
+ *   U      device FP64 [ne][5][nb] coefficients (any element order);
+ *   detJ   device FP64 [ne], |det J| of each tetrahedron, same order;
+ *   totals device FP64 [5], written.
+ * It allocates nothing: the per-block partial sums live in one fixed 40 KB
+ * device array inside the library (every GPU that loads the library keeps it
+ * until the process exits), so ne is limited to 4,194,304 elements (4096 per
+ * block, 1024 blocks); larger ne returns DG_ERR_ARG.  Each call overwrites
+ * every partial sum it reads, so nothing needs clearing between calls; calls
+ * that overlap on the GPU (different streams, or different host threads) race
+ * on the shared array and must be serialised by the caller.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.
+ * Asynchronous on `stream`. */
+dg_status dg_conserved_totals_noalloc(const double* U, const double* detJ, int64_t ne, int nb, double* totals,
+                                      void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* dg_last_error(void);
 

@@ -63,6 +63,10 @@ constexpr int RED_SLOTS = 1024 * 6;   // per-block partials; results follow
 
 }  // namespace
 
+namespace dg {
+dg_status set_error(dg_status code, const char* msg) { return fail(code, msg); }
+}  // namespace dg
+
 size_t dg_mesh::state_bytes() const { return (size_t)host.ne * 5 * nb * real_size(precision); }
 
 extern "C" {

@@ -137,5 +137,6 @@ cudaError_t launch_residual_mixed(dg_mesh* m, const float* U_hi, const float* U_
                                   const float* U0_lo, float* out_hi, float* out_lo, int mode, double dt, double a,
                                   double b, cudaStream_t s);
 void build_mixed_tables(int p, const RefData& ref, std::vector<uint16_t>& out, float& inv_b1, float& inv_b2);
+dg_status set_error(dg_status code, const char* msg);   // sets dg_last_error() for the calling thread
 int mixed_tab_halves(int p);
 }  // namespace dg

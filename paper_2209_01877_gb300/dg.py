@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_MESH", 3: "DG_ERR_CUDA",
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_sizes", "dg_volume_points", "dg_project",
             "dg_set_state", "dg_get_state", "dg_residual", "dg_rk_stage", "dg_rk3_step", "dg_stable_dt",
             "dg_integrals", "dg_residual_vjp", "dg_rk3_step_vjp", "dg_kinetic_energy_grad", "dg_sync_status",
-            "dg_reference_data",
+            "dg_reference_data", "dg_conserved_totals_noalloc",
             "dg_last_error"]
 
 
@@ -73,6 +73,7 @@ def load():
             "dg_kinetic_energy_grad": [vp, vp, vp, vp],
             "dg_sync_status": [vp, vp],
             "dg_reference_data": [C.c_int, vp, vp, vp, vp, vp, vp],
+            "dg_conserved_totals_noalloc": [vp, vp, i64, C.c_int, vp, vp],
         }
         for name, args in sigs.items():
             fn = getattr(lib, name)
@@ -240,6 +241,14 @@ def dg_reference_data(order):
     ptrs = [C.c_void_p(a.ctypes.data) for a in out.values()]
     _check(load().dg_reference_data(int(order), *ptrs))
     return out
+
+
+def dg_conserved_totals_noalloc(U, detJ, totals, stream=None, ne=None):
+    """Allocation-free conserved totals: U [ne][5][nb], detJ [ne], totals [5],
+    all float64 CUDA tensors owned by the caller."""
+    n = int(U.shape[0]) if ne is None else int(ne)
+    _check(load().dg_conserved_totals_noalloc(_dptr(U), _dptr(detJ), n, int(U.shape[2]), _dptr(totals),
+                                              _stream(stream)))
 
 
 def dg_last_error():
