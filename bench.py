@@ -368,6 +368,71 @@ def config_of(args):
             else "state fits in L2 (small case)"}
 
 
+def run_study(args):
+    """Studies of the paper's two optimisations, printed as one JSON object.
+
+    temporal-mp  (Sec. III-B, Tab. 2): n steps with the first k in FP32 and the
+                 rest in FP64, k = 0, 20%, 50%, 80%, 100% of n; device time and
+                 the RMS coefficient difference from the all-FP64 run.
+    renumbering  (Sec. III-B, Tab. 1): element-adjacency bandwidth and RK-step
+                 throughput for the input (random) order, RCM and Morton."""
+    import torch
+    from paper_2209_01877_gb300 import dg
+    from paper_2209_01877_gb300.temporal import run_temporal_mp
+    torch.cuda.set_device(0)
+    mesh, field, w = make_workload(args.workload)
+    p, flux = w["p"], w["flux"]
+    fl = dg.DG_ROE if flux == "roe" else dg.DG_RUSANOV
+    tag = mesh.bc_tag if w["box"] else None
+    fs = (0, 0, 0, 0, 0)
+    if w["box"]:
+        from paper_2209_01877_gb300 import inputs as I
+        fs = tuple(I.freestream_state(0.3))
+    out = {"study": args.study, "workload": config_of(args)["workload"]}
+    if args.study == "temporal-mp":
+        m64 = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, tag, order=p, precision=dg.DG_FP64, flux=fl, freestream=fs)
+        m32 = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, tag, order=p, precision=dg.DG_FP32, flux=fl, freestream=fs)
+        U0 = torch.from_numpy(m64.project(field)).cuda()
+        dg.dg_set_state(m64.handle, U0)
+        dt = dg.dg_stable_dt(m64.handle, 0.1)
+        n = args.steps
+        run_temporal_mp(m32, m64, U0, dt, 1, 1)          # warm-up of both paths
+        run_temporal_mp(m32, m64, U0, dt, 1, 0)
+        ref, _, t_ref = run_temporal_mp(m32, m64, U0, dt, n, 0)
+        rows = []
+        for frac in (0.0, 0.2, 0.5, 0.8, 1.0):
+            k = int(round(frac * n))
+            U, t_sp, t_dp = run_temporal_mp(m32, m64, U0, dt, n, k)
+            rows.append({"sp_steps": k, "dp_steps": n - k, "seconds": t_sp + t_dp,
+                         "rms_diff_vs_dp": float(((U - ref) ** 2).mean().sqrt())})
+        out.update({"steps": n, "dt": dt, "rows": rows})
+    else:
+        rows = []
+        for name, order in (("input (random)", dg.DG_ORDER_ASIS), ("RCM", dg.DG_ORDER_RCM),
+                            ("Morton", dg.DG_ORDER_MORTON)):
+            prec = {"fp64": dg.DG_FP64, "fp32": dg.DG_FP32}.get(args.precision, dg.DG_MIXED_FP16)
+            M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, tag, order=p, precision=prec, flux=fl, renumber=order,
+                        freestream=fs)
+            info = M.info()
+            U0 = M.project(field)
+            dg.dg_set_state(M.handle, U0)
+            dt = dg.dg_stable_dt(M.handle, 0.1)
+            dg.dg_rk3_step(M.handle, dt, 3)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dg.dg_rk3_step(M.handle, dt, args.steps)
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3
+            rows.append({"order": name, "bandwidth": info["bandwidth_after"],
+                         "dof_updates_per_s": 3 * mesh.ne * 5 * NB[p] * args.steps / t,
+                         "ms_per_step": t / args.steps * 1e3})
+            M.close()
+        out.update({"precision": args.precision, "rows": rows})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,6 +441,8 @@ def main():
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64", "fp32"])
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 comparison leg of a mixed run")
+    ap.add_argument("--study", choices=["temporal-mp", "renumbering"], default=None,
+                    help="print a study table instead of the benchmark line")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -387,6 +454,9 @@ def main():
         run_reference(args)
         return
 
+    if args.study:
+        run_study(args)
+        return
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

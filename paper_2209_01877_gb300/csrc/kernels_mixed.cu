@@ -66,9 +66,11 @@ struct MixPlan {
     static constexpr int KL2 = 3 * NQP + 4 * NQFP;  // logical (k, q) then (f, q)
     static constexpr int K2 = r16(2 * KL2);
     static constexpr int N2 = r16(NB);
-    // tensor-memory columns
-    static constexpr int C1 = 0, C1B = r32(N1), C2 = r32(C1B + 4 * N1B);
-    static_assert(C2 + N2 <= TMEM_COLS, "tensor memory");
+    // tensor-memory columns: D1 (own points, image a), D1b[4] (neighbour traces), D2[4] (four
+    // independent partial projections over quarters of K, summed in the epilogue), D1' (own
+    // points, image b) -- independent accumulators shorten the dependent MMA chains
+    static constexpr int C1 = 0, C1B = r32(N1), C2 = r32(C1B + 4 * N1B), C1X = r32(C2 + 4 * N2);
+    static_assert(C1X + N1 <= TMEM_COLS, "tensor memory");
     // shared-memory layout (bytes)
     static constexpr int SZ_B1 = 2 * N1 * K1 * 2, SZ_B2 = 2 * N2 * K2 * 2;   // two table images each
     static constexpr int SZ_A1 = 128 * K1 * 2, SZ_A1B = 4 * SZ_A1, SZ_A2 = 128 * K2 * 2;
@@ -84,7 +86,9 @@ struct MixPlan {
     static constexpr int O_NB = O_SN + ET * 4 * 4;            // int [ET][4]
     static constexpr int O_FC = O_NB + ET * 4 * 4;            // uint8 [ET][4]
     static constexpr int O_IP = O_FC + ET * 4;                // int8 [6][NQF] inverse face permutation
-    static constexpr int O_MB = (O_IP + 6 * NQF + 15) / 16 * 16;   // mbarrier + tmem slot
+    static constexpr int SZ_PF = (ET * 5 * NB * 4 + 15) / 16 * 16;   // one tile plane of the state
+    static constexpr int O_PF = (O_IP + 6 * NQF + 15) / 16 * 16;     // prefetched U_hi, U_lo, U0_hi, U0_lo
+    static constexpr int O_MB = O_PF + 4 * SZ_PF;                    // mbarrier + tmem slot
     static constexpr int BYTES = O_MB + 32;
     // f16 table image in global memory: B1a, B1b, B2a, B2b (canonical order)
     static constexpr int TAB_HALVES = 2 * N1 * K1 + 2 * N2 * K2;
@@ -185,6 +189,7 @@ __global__ void __launch_bounds__(MT, 1) k_residual_mixed(MixArgs<float> a) {
     int* sNb = reinterpret_cast<int*>(smem + S::O_NB);
     uint8_t* sFc = reinterpret_cast<uint8_t*>(smem + S::O_FC);
     int8_t* sIp = reinterpret_cast<int8_t*>(smem + S::O_IP);
+    float* sPf = reinterpret_cast<float*>(smem + S::O_PF);           // [4][ET*5*NB] tile planes
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::O_MB);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::O_MB + 8);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -222,10 +227,11 @@ __global__ void __launch_bounds__(MT, 1) k_residual_mixed(MixArgs<float> a) {
             sFc[i] = a.fcode[e0 * 4 + i];
         }
         for (int i = tid; i < nel * 9; i += MT) sJi[i] = a.jinv[e0 * 9 + i];
+        __syncthreads();
         for (int i = tid; i < nel * 5; i += MT) {
             // i < nel: element i itself; nel <= i < 5 nel: neighbour slot (e, f) = i - nel
             const int e = i < nel ? i : (i - nel) >> 2, slot = i < nel ? 0 : 1 + ((i - nel) & 3);
-            const int n = slot == 0 ? (int)(e0 + e) : a.nbr[(e0 + e) * 4 + slot - 1];
+            const int n = slot == 0 ? (int)(e0 + e) : sNb[e * 4 + slot - 1];
             float ub[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
             if (n >= 0) {
                 const float* c = a.U_hi + (int64_t)n * 5 * NB;
@@ -243,7 +249,7 @@ __global__ void __launch_bounds__(MT, 1) k_residual_mixed(MixArgs<float> a) {
             const float vel[3] = {ub[1] * ri, ub[2] * ri, ub[3] * ri};
             const float pr = (gamma - 1.f) * (ub[4] - 0.5f * (ub[1] * vel[0] + ub[2] * vel[1] + ub[3] * vel[2]));
             const float spd = sqrtf(vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]) + sqrtf(fabsf(gamma * pr * ri));
-            const float* I = a.jinv + (e0 + e) * 9;
+            const float* I = sJi + e * 9;
             float ih = 0.f;
             for (int f = 0; f < 4; ++f) {
                 float g0, g1, g2;
@@ -263,33 +269,64 @@ __global__ void __launch_bounds__(MT, 1) k_residual_mixed(MixArgs<float> a) {
                 F[4] = (ub[4] + pr) * vel[d];
             }
         }
+        // ---- asynchronous copies of this tile's planes: U_hi (operand A1 and the RK update), and in
+        // RK mode U_lo, U0_hi, U0_lo (16-byte units; a partial last unit reads into the next plane or
+        // the buffer slack)
+        {
+            const int units = (nel * 5 * NB * 4 + 15) / 16;
+            const int nplanes = a.mode == 0 ? 1 : (a.a_hi != 0.f ? 4 : 2);
+            for (int i = tid; i < nplanes * units; i += MT) {
+                const int pl = i / units, u = i - pl * units;
+                const float* src = pl == 0 ? a.U_hi : (pl == 1 ? a.U_lo : (pl == 2 ? a.U0_hi : a.U0_lo));
+                tc::cp_async16(reinterpret_cast<char*>(sPf) + pl * S::SZ_PF + 16 * u,
+                               reinterpret_cast<const char*>(src + e0 * 5 * NB) + 16 * u);
+            }
+            tc::cp_async_commit();
+        }
         __syncthreads();
         // ---- split-f16 operands A1 (own) and A1b[f] (neighbours), modes 1.. only -----------------
-        // item = (slot, e, v, chunk of 4 modes): 4 interleaved (hi, lo) pairs = one 16-byte store
-        for (int i = tid; i < 5 * nel * 5 * NBC; i += MT) {
-            const int slot = i / (nel * 5 * NBC), rem = i - slot * (nel * 5 * NBC);
-            const int r = rem / NBC, cch = rem - r * NBC;   // r = e*5 + v
-            const int e = r / 5;
-            int n;
-            float sc;
-            if (slot == 0) {
-                n = (int)(e0 + e);
-                sc = sSc[2 * e];
-            } else {
-                n = sNb[e * 4 + slot - 1];
-                sc = sSn[e * 4 + slot - 1];
-            }
-            uint32_t w[4] = {0u, 0u, 0u, 0u};
-            if (n >= 0) {
-                const float* c = a.U_hi + (int64_t)n * 5 * NB + (r - 5 * e) * NB;
+        // item = (slot, e, v, chunk of 4 modes): 4 interleaved (hi, lo) pairs = one 16-byte store.
+        // Each thread first gathers the coefficients of all its items, then converts and stores.
+        {
+            constexpr int PER_SLOT = ET * 5 * NBC;
+            constexpr int MAXIT = (5 * PER_SLOT + MT - 1) / MT;
+            float x[MAXIT][4];
+#pragma unroll
+            for (int it = 0; it < MAXIT; ++it) {
+                const int i = tid + it * MT;
+                x[it][0] = x[it][1] = x[it][2] = x[it][3] = 0.f;
+                const int slot = i / PER_SLOT, rem = i - slot * PER_SLOT;
+                const int r = rem / NBC, cch = rem - r * NBC;
+                const int e = r / 5, v = r - 5 * e;
+                if (slot >= 5 || e >= nel) continue;
+                const float* c;
+                if (slot == 0) {
+                    c = a.U_hi + (e0 * 5 + r) * NB;
+                } else {
+                    const int n = sNb[e * 4 + slot - 1];
+                    if (n < 0) continue;
+                    c = a.U_hi + (int64_t)n * 5 * NB + v * NB;
+                }
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const int j = cch * 4 + t;
-                    if (j >= 1 && j < NB) w[t] = split_pair(c[j] * sc);
+                    if (j >= 1 && j < NB) x[it][t] = c[j];
                 }
             }
-            __half* A = slot == 0 ? sA1 : sA1b + (slot - 1) * 128 * K1;
-            *reinterpret_cast<uint4*>(A + tc::kmajor(r, 8 * cch, K1)) = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+            for (int it = 0; it < MAXIT; ++it) {
+                const int i = tid + it * MT;
+                const int slot = i / PER_SLOT, rem = i - slot * PER_SLOT;
+                const int r = rem / NBC, cch = rem - r * NBC;
+                const int e = r / 5;
+                if (slot >= 5 || e >= nel) continue;
+                const float sc = slot == 0 ? sSc[2 * e] : sSn[e * 4 + slot - 1];
+                uint32_t w[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) w[t] = x[it][t] != 0.f ? split_pair(x[it][t] * sc) : 0u;
+                __half* A = slot == 0 ? sA1 : sA1b + (slot - 1) * 128 * K1;
+                *reinterpret_cast<uint4*>(A + tc::kmajor(r, 8 * cch, K1)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
         }
         tc::fence_async_smem();
         tc::fence_before();
@@ -303,8 +340,8 @@ __global__ void __launch_bounds__(MT, 1) k_residual_mixed(MixArgs<float> a) {
             for (int h = 0; h < 2; ++h)
 #pragma unroll
                 for (int ks = 0; ks < K1 / 16; ++ks)
-                    tc::mma(tmem + S::C1, tc::kdesc(sA1, ks, K1), tc::kdesc(h ? sB1b : sB1a, ks, K1), id1,
-                            (h | ks) != 0);
+                    tc::mma(tmem + (h ? S::C1X : S::C1), tc::kdesc(sA1, ks, K1), tc::kdesc(h ? sB1b : sB1a, ks, K1),
+                            id1, ks != 0);
 #pragma unroll
             for (int f = 0; f < 4; ++f)
 #pragma unroll
@@ -316,7 +353,9 @@ __global__ void __launch_bounds__(MT, 1) k_residual_mixed(MixArgs<float> a) {
             tc::commit(mbar);
         }
         {
-            const bool ok = tc::mbar_wait(mbar, phase, WAIT_ITERS);
+            // one thread polls the barrier; the other warps wait at the block barrier, which costs
+            // no issue slots
+            const bool ok = tid == 0 ? tc::mbar_wait(mbar, phase, WAIT_ITERS) : true;
             phase ^= 1u;
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) atomicOr(a.status, 2u);
@@ -334,13 +373,28 @@ __global__ void __launch_bounds__(MT, 1) k_residual_mixed(MixArgs<float> a) {
             constexpr int CW = (N1 / 4 + 3) / 4 * 4;
             const float inv_own = row_ok ? a.inv_beta1 / sSc[2 * e] : 0.f;
             const float ub_own = row_ok ? sUb[(e * 5) * 5 + v] : 0.f;
-            for (int c0 = part * CW; c0 < (part + 1) * CW && c0 < N1; c0 += 4) {
-                float val[4];
-                tc::ld4(tmem + lane_base + S::C1 + c0, val);
-                if (row_ok) {
+            {
+                int c0 = part * CW;
+                const int c1 = (part + 1) * CW < N1 ? (part + 1) * CW : N1;
+                for (; c0 + 16 <= c1; c0 += 16) {
+                    float val[16], vx[16];
+                    tc::ld16(tmem + lane_base + S::C1 + c0, val);
+                    tc::ld16(tmem + lane_base + S::C1X + c0, vx);
+                    if (row_ok) {
 #pragma unroll
-                    for (int t = 0; t < 4; ++t)
-                        if (c0 + t < NPT) sUq[(e * NPT + c0 + t) * 5 + v] = fmaf(val[t], inv_own, ub_own);
+                        for (int t = 0; t < 16; ++t)
+                            if (c0 + t < NPT) sUq[(e * NPT + c0 + t) * 5 + v] = fmaf(val[t] + vx[t], inv_own, ub_own);
+                    }
+                }
+                for (; c0 < c1; c0 += 4) {
+                    float val[4], vx[4];
+                    tc::ld4(tmem + lane_base + S::C1 + c0, val);
+                    tc::ld4(tmem + lane_base + S::C1X + c0, vx);
+                    if (row_ok) {
+#pragma unroll
+                        for (int t = 0; t < 4; ++t)
+                            if (c0 + t < NPT) sUq[(e * NPT + c0 + t) * 5 + v] = fmaf(val[t] + vx[t], inv_own, ub_own);
+                    }
                 }
             }
             // neighbour across face `part`: its trace in its own face-point order
@@ -351,8 +405,22 @@ __global__ void __launch_bounds__(MT, 1) k_residual_mixed(MixArgs<float> a) {
             const int fn = code & 3, oc = code >> 2;
             const float inv = (row_ok && n >= 0) ? a.inv_beta1 / sSn[ef] : 0.f;
             const float ubn = row_ok ? sUb[(e * 5 + 1 + f) * 5 + v] : 0.f;
+            constexpr int NF16 = NF / 16 * 16;
 #pragma unroll
-            for (int c0 = 0; c0 < NF; c0 += 4) {
+            for (int c0 = 0; c0 < NF16; c0 += 16) {
+                float val[16];
+                tc::ld16(tmem + lane_base + S::C1B + f * N1B + c0, val);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int c = c0 + t;
+                    if (n >= 0 && c / NQF == fn) {
+                        const int q = sIp[oc * NQF + (c - fn * NQF)];
+                        sUp[(ef * NQF + q) * 5 + v] = fmaf(val[t], inv, ubn);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c0 = NF16; c0 < NF; c0 += 4) {
                 float val[4];
                 tc::ld4(tmem + lane_base + S::C1B + f * N1B + c0, val);
 #pragma unroll
@@ -367,101 +435,104 @@ __global__ void __launch_bounds__(MT, 1) k_residual_mixed(MixArgs<float> a) {
         }
         tc::fence_before();
         __syncthreads();
-        // ---- volume points, 4 per item: (F - F_mean) -> contravariant -> A2 (16-byte stores) -----
-        constexpr int QC = NQP / 4;
-        for (int i = tid; i < nel * QC; i += MT) {
-            const int e = i / QC, q0 = (i - e * QC) * 4;
-            const float* I = sJi + e * 9;
-            const float* Fb = sFb + e * 15;
-            const float ts = sSc[2 * e + 1];
-            uint32_t w[3][5][4];
+        // ---- fluxes: items of 2 points; volume items first, then face items ---------------------
+        // volume: (F - F_mean) -> contravariant -> A2 at (k, q); face: Riemann flux - F_mean.n at (f, q)
+        constexpr int QC = NQP / 2, FC = NQFP / 2;
+        for (int i = tid; i < ET * (QC + 4 * FC); i += MT) {
+            if (i < ET * QC) {
+                const int e = i / QC, q0 = (i - e * QC) * 2;
+                if (e >= nel) continue;
+                const float* I = sJi + e * 9;
+                const float* Fb = sFb + e * 15;
+                const float ts = sSc[2 * e + 1];
+                uint32_t w[3][5][2];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int q = q0 + t;
-                if (q >= NQ) {
+                for (int t = 0; t < 2; ++t) {
+                    const int q = q0 + t;
+                    if (q >= NQ) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k)
+#pragma unroll
+                            for (int v = 0; v < 5; ++v) w[k][v][t] = 0u;
+                        continue;
+                    }
+                    const float* u = sUq + (e * NPT + NF + q) * 5;
+                    float U[5] = {u[0], u[1], u[2], u[3], u[4]};
+                    if (!physical(U, gamma)) atomicOr(a.status, 1u);
+                    const float ri = 1.f / U[0];
+                    const float vel[3] = {U[1] * ri, U[2] * ri, U[3] * ri};
+                    const float p = (gamma - 1.f) * (U[4] - 0.5f * (U[1] * vel[0] + U[2] * vel[1] + U[3] * vel[2]));
+                    float F[3][5];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        F[d][0] = U[1 + d] - Fb[d * 5 + 0];
+                        F[d][1] = U[1] * vel[d] - Fb[d * 5 + 1];
+                        F[d][2] = U[2] * vel[d] - Fb[d * 5 + 2];
+                        F[d][3] = U[3] * vel[d] - Fb[d * 5 + 3];
+                        F[d][1 + d] += p;
+                        F[d][4] = (U[4] + p) * vel[d] - Fb[d * 5 + 4];
+                    }
 #pragma unroll
                     for (int k = 0; k < 3; ++k)
 #pragma unroll
-                        for (int v = 0; v < 5; ++v) w[k][v][t] = 0u;
-                    continue;
-                }
-                const float* u = sUq + (e * NPT + NF + q) * 5;
-                float U[5] = {u[0], u[1], u[2], u[3], u[4]};
-                if (!physical(U, gamma)) atomicOr(a.status, 1u);
-                const float ri = 1.f / U[0];
-                const float vel[3] = {U[1] * ri, U[2] * ri, U[3] * ri};
-                const float p = (gamma - 1.f) * (U[4] - 0.5f * (U[1] * vel[0] + U[2] * vel[1] + U[3] * vel[2]));
-                float F[3][5];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    F[d][0] = U[1 + d] - Fb[d * 5 + 0];
-                    F[d][1] = U[1] * vel[d] - Fb[d * 5 + 1];
-                    F[d][2] = U[2] * vel[d] - Fb[d * 5 + 2];
-                    F[d][3] = U[3] * vel[d] - Fb[d * 5 + 3];
-                    F[d][1 + d] += p;
-                    F[d][4] = (U[4] + p) * vel[d] - Fb[d * 5 + 4];
+                        for (int v = 0; v < 5; ++v)
+                            w[k][v][t] = split_pair(ts * (I[3 * k] * F[0][v] + I[3 * k + 1] * F[1][v] + I[3 * k + 2] * F[2][v]));
                 }
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
 #pragma unroll
                     for (int v = 0; v < 5; ++v)
-                        w[k][v][t] = split_pair(ts * (I[3 * k] * F[0][v] + I[3 * k + 1] * F[1][v] + I[3 * k + 2] * F[2][v]));
-            }
+                        *reinterpret_cast<uint2*>(sA2 + tc::kmajor(e * 5 + v, 2 * (k * NQP + q0), K2)) =
+                            make_uint2(w[k][v][0], w[k][v][1]);
+            } else {
+                const int j = i - ET * QC;
+                const int ef = j / FC, q0 = (j - ef * FC) * 2;
+                const int e = ef >> 2, f = ef & 3;
+                if (e >= nel) continue;
+                const float* I = sJi + e * 9;
+                float g0, g1, g2;
+                grad_lambda(I, f, g0, g1, g2);
+                const float s = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
+                const float ninv = -1.f / s;
+                const float nv[3] = {g0 * ninv, g1 * ninv, g2 * ninv};
+                const float* Fb = sFb + e * 15;
+                float Fbn[5];
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
+                for (int v = 0; v < 5; ++v) Fbn[v] = Fb[v] * nv[0] + Fb[5 + v] * nv[1] + Fb[10 + v] * nv[2];
+                const int n = sNb[ef];
+                const float sc = -s * sSc[2 * e + 1];
+                uint32_t w[5][2];
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int q = q0 + t;
+                    if (q >= NQF) {
+#pragma unroll
+                        for (int v = 0; v < 5; ++v) w[v][t] = 0u;
+                        continue;
+                    }
+                    const float* um = sUq + (e * NPT + f * NQF + q) * 5;
+                    float Um[5] = {um[0], um[1], um[2], um[3], um[4]}, Up[5];
+                    if (n >= 0) {
+                        const float* up = sUp + (ef * NQF + q) * 5;
+#pragma unroll
+                        for (int v = 0; v < 5; ++v) Up[v] = up[v];
+                    } else if (n == -1 - DG_BC_WALL) {
+                        wall_ghost(Um, nv, Up);
+                    } else {
+                        farfield_ghost(Um, nv, a.finf, gamma, Up);
+                    }
+                    if (!physical(Um, gamma)) atomicOr(a.status, 1u);
+                    float H[5];
+                    if (FLUX == DG_ROE) roe_flux(Um, Up, nv, gamma, a.roe_eps, H);
+                    else rusanov_flux(Um, Up, nv, gamma, H);
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) w[v][t] = split_pair(sc * (H[v] - Fbn[v]));
+                }
 #pragma unroll
                 for (int v = 0; v < 5; ++v)
-                    *reinterpret_cast<uint4*>(sA2 + tc::kmajor(e * 5 + v, 2 * (k * NQP + q0), K2)) =
-                        make_uint4(w[k][v][0], w[k][v][1], w[k][v][2], w[k][v][3]);
-        }
-        // ---- face points, 4 per item: Riemann flux - F_mean.n -> A2 ------------------------------
-        constexpr int FC = NQFP / 4;
-        for (int i = tid; i < nel * 4 * FC; i += MT) {
-            const int ef = i / FC, q0 = (i - ef * FC) * 4;
-            const int e = ef >> 2, f = ef & 3;
-            const float* I = sJi + e * 9;
-            float g0, g1, g2;
-            grad_lambda(I, f, g0, g1, g2);
-            const float s = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
-            const float ninv = -1.f / s;
-            const float nv[3] = {g0 * ninv, g1 * ninv, g2 * ninv};
-            const float* Fb = sFb + e * 15;
-            float Fbn[5];
-#pragma unroll
-            for (int v = 0; v < 5; ++v) Fbn[v] = Fb[v] * nv[0] + Fb[5 + v] * nv[1] + Fb[10 + v] * nv[2];
-            const int n = sNb[ef];
-            const float sc = -s * sSc[2 * e + 1];
-            uint32_t w[5][4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int q = q0 + t;
-                if (q >= NQF) {
-#pragma unroll
-                    for (int v = 0; v < 5; ++v) w[v][t] = 0u;
-                    continue;
-                }
-                const float* um = sUq + (e * NPT + f * NQF + q) * 5;
-                float Um[5] = {um[0], um[1], um[2], um[3], um[4]}, Up[5];
-                if (n >= 0) {
-                    const float* up = sUp + (ef * NQF + q) * 5;
-#pragma unroll
-                    for (int v = 0; v < 5; ++v) Up[v] = up[v];
-                } else if (n == -1 - DG_BC_WALL) {
-                    wall_ghost(Um, nv, Up);
-                } else {
-                    farfield_ghost(Um, nv, a.finf, gamma, Up);
-                }
-                if (!physical(Um, gamma)) atomicOr(a.status, 1u);
-                float H[5];
-                if (FLUX == DG_ROE) roe_flux(Um, Up, nv, gamma, a.roe_eps, H);
-                else rusanov_flux(Um, Up, nv, gamma, H);
-#pragma unroll
-                for (int v = 0; v < 5; ++v) w[v][t] = split_pair(sc * (H[v] - Fbn[v]));
+                    *reinterpret_cast<uint2*>(sA2 + tc::kmajor(e * 5 + v, 2 * (3 * NQP + f * NQFP + q0), K2)) =
+                        make_uint2(w[v][0], w[v][1]);
             }
-#pragma unroll
-            for (int v = 0; v < 5; ++v)
-                *reinterpret_cast<uint4*>(sA2 + tc::kmajor(e * 5 + v, 2 * (3 * NQP + f * NQFP + q0), K2)) =
-                    make_uint4(w[v][0], w[v][1], w[v][2], w[v][3]);
         }
         // rows of elements beyond the tile end keep finite stale values (their outputs are
         // discarded); padded K positions meet zero table entries
@@ -472,17 +543,24 @@ __global__ void __launch_bounds__(MT, 1) k_residual_mixed(MixArgs<float> a) {
         // ---- MMA 2: projection onto the weighted basis gradients + face lift ----------------------
         if (tid == 0) {
             const uint32_t id2 = tc::idesc_f16(128, N2);
+            constexpr int KS = K2 / 16;
 #pragma unroll 1
-            for (int h = 0; h < 2; ++h)
-#pragma unroll 1
-                for (int ks = 0; ks < K2 / 16; ++ks)
-                    tc::mma(tmem + S::C2, tc::kdesc(sA2, ks, K2), tc::kdesc(h ? sB2b : sB2a, ks, K2), id2,
-                            (h | ks) != 0);
+            for (int ks = 0; ks < KS; ++ks) {
+                const int part = ks * 4 / KS;   // four contiguous K ranges -> four accumulators
+                const int first = (part * KS + 3) / 4;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    tc::mma(tmem + S::C2 + part * N2, tc::kdesc(sA2, ks, K2), tc::kdesc(h ? sB2b : sB2a, ks, K2), id2,
+                            (h != 0 || ks != first) ? 1u : 0u);
+            }
             tc::commit(mbar);
         }
         {
-            const bool ok = tc::mbar_wait(mbar, phase, WAIT_ITERS);
+            // one thread polls the barrier; the other warps wait at the block barrier, which costs
+            // no issue slots
+            const bool ok = tid == 0 ? tc::mbar_wait(mbar, phase, WAIT_ITERS) : true;
             phase ^= 1u;
+            tc::cp_async_wait_all();   // this thread's copies of the tile planes have landed
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) atomicOr(a.status, 2u);
                 break;
@@ -499,8 +577,14 @@ __global__ void __launch_bounds__(MT, 1) k_residual_mixed(MixArgs<float> a) {
             constexpr int CW = (N2 / 4 + 3) / 4 * 4;
             const float inv = row_ok ? a.inv_beta2 / sSc[2 * e + 1] : 0.f;
             for (int c0 = part * CW; c0 < (part + 1) * CW && c0 < N2; c0 += 4) {
-                float val[4];
+                float val[4], vp[4];
                 tc::ld4(tmem + lane_base + S::C2 + c0, val);
+#pragma unroll
+                for (int pp = 1; pp < 4; ++pp) {
+                    tc::ld4(tmem + lane_base + S::C2 + pp * N2 + c0, vp);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) val[t] += vp[t];
+                }
                 if (!row_ok) continue;
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
@@ -511,13 +595,15 @@ __global__ void __launch_bounds__(MT, 1) k_residual_mixed(MixArgs<float> a) {
                     if (a.mode == 0) {
                         a.out_hi[gi] = R;
                     } else {
-                        const ff Ucur = {a.U_hi[gi], a.U_lo[gi]};
+                        const int li = (e * 5 + v) * NB + j;   // tile-local index of the prefetched planes
+                        const ff Ucur = {sPf[li], sPf[S::SZ_PF / 4 + li]};
                         const float pr = a.dt_hi * R;
                         float er = fmaf(a.dt_hi, R, -pr);
                         er = fmaf(a.dt_lo, R, er);
                         ff t1 = ff_add(Ucur, ff{pr, er});
                         if (a.a_hi != 0.f) {
-                            const ff U0 = {a.U0_hi[gi], a.U0_lo[gi]};
+                            const float* pf = sPf + 2 * (S::SZ_PF / 4);
+                            const ff U0 = {pf[li], pf[S::SZ_PF / 4 + li]};
                             t1 = ff_add(ff_mul(ff{a.a_hi, a.a_lo}, U0), ff_mul(ff{a.b_hi, a.b_lo}, t1));
                         }
                         a.out_hi[gi] = t1.h;
