@@ -375,7 +375,11 @@ def run_study(args):
                  rest in FP64, k = 0, 20%, 50%, 80%, 100% of n; device time and
                  the RMS coefficient difference from the all-FP64 run.
     renumbering  (Sec. III-B, Tab. 1): element-adjacency bandwidth and RK-step
-                 throughput for the input (random) order, RCM and Morton."""
+                 throughput for the input (random) order, RCM and Morton.
+    adjoint      residual VJP and RK-step VJP throughput, and the checkpointed
+                 multi-step adjoint (steps = --steps, checkpoints every 10).
+    aux          the time-step reduction and the conservation / kinetic-energy
+                 sums (device time per call)."""
     import torch
     from paper_2209_01877_gb300 import dg
     from paper_2209_01877_gb300.temporal import run_temporal_mp
@@ -406,6 +410,60 @@ def run_study(args):
             rows.append({"sp_steps": k, "dp_steps": n - k, "seconds": t_sp + t_dp,
                          "rms_diff_vs_dp": float(((U - ref) ** 2).mean().sqrt())})
         out.update({"steps": n, "dt": dt, "rows": rows})
+    elif args.study == "adjoint":
+        from paper_2209_01877_gb300.adjoint import rk3_adjoint
+        prec = {"fp32": dg.DG_FP32}.get(args.precision, dg.DG_FP64)
+        M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, tag, order=p, precision=prec, flux=fl, freestream=fs)
+        U0 = torch.from_numpy(M.project(field)).cuda()
+        dg.dg_set_state(M.handle, U0)
+        dt = dg.dg_stable_dt(M.handle, 0.1)
+        lam = torch.ones_like(U0)
+        out_t = torch.empty_like(U0)
+        dofs = mesh.ne * 5 * NB[p]
+
+        def timed(fn, reps):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / 1e3 / reps
+
+        t_res = timed(lambda: dg.dg_residual(M.handle, U0, out_t), 5)
+        t_vjp = timed(lambda: dg.dg_residual_vjp(M.handle, U0, lam, out_t), 5)
+        t_svjp = timed(lambda: dg.dg_rk3_step_vjp(M.handle, U0, dt, lam, out_t), 3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, g, peak = rk3_adjoint(M, U0, dt, args.steps, ckpt_every=10)
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        out.update({"precision": "f32" if prec == dg.DG_FP32 else "f64", "dofs": dofs,
+                    "residual_ms": t_res * 1e3, "residual_vjp_ms": t_vjp * 1e3,
+                    "residual_vjp_dof_per_s": dofs / t_vjp, "rk3_step_vjp_ms": t_svjp * 1e3,
+                    "adjoint_steps": args.steps, "adjoint_seconds": t_adj, "adjoint_peak_states": peak,
+                    "kinetic_energy": J})
+    elif args.study == "aux":
+        prec = {"fp64": dg.DG_FP64, "fp32": dg.DG_FP32}.get(args.precision, dg.DG_MIXED_FP16)
+        M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, tag, order=p, precision=prec, flux=fl, freestream=fs)
+        dg.dg_set_state(M.handle, M.project(field))
+        for _ in range(3):
+            dg.dg_stable_dt(M.handle, 0.1)
+            dg.dg_integrals(M.handle)
+        n = max(args.steps, 5)
+        t0 = time.perf_counter()
+        for _ in range(n):
+            dg.dg_stable_dt(M.handle, 0.1)
+        t_dt = (time.perf_counter() - t0) / n
+        t0 = time.perf_counter()
+        for _ in range(n):
+            dg.dg_integrals(M.handle)
+        t_int = (time.perf_counter() - t0) / n
+        out.update({"stable_dt_ms_incl_sync": t_dt * 1e3, "integrals_ms_incl_sync": t_int * 1e3,
+                    "tets": mesh.ne})
     else:
         rows = []
         for name, order in (("input (random)", dg.DG_ORDER_ASIS), ("RCM", dg.DG_ORDER_RCM),
@@ -441,7 +499,7 @@ def main():
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64", "fp32"])
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 comparison leg of a mixed run")
-    ap.add_argument("--study", choices=["temporal-mp", "renumbering"], default=None,
+    ap.add_argument("--study", choices=["temporal-mp", "renumbering", "adjoint", "aux"], default=None,
                     help="print a study table instead of the benchmark line")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
