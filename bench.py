@@ -57,6 +57,19 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def replica_value(work_per_rank, t_local, world, device=None):
+    """Whole-job throughput of independent replicas: every rank did
+    ``work_per_rank`` units; the job time is the slowest rank's (all-reduce MAX
+    over the process group when world > 1)."""
+    t = t_local
+    if world > 1:
+        import torch
+        x = torch.tensor([t_local], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+        t = float(x.item())
+    return t, world * work_per_rank / t
+
+
 def make_workload(name):
     from paper_2209_01877_gb300 import inputs as I
     w = WORKLOADS[name]
@@ -217,12 +230,8 @@ def run_ours(args, rank, world, device):
     for i, (a, b) in enumerate(ev):
         stage_ms[i % 3].append(a.elapsed_time(b))
     t_local = t_total
-    if world > 1:
-        t = torch.tensor([t_total], device=device, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total, value = replica_value(3 * dofs * args.steps, t_local, world, device)
     ms_per_step = t_total / args.steps * 1e3
-    value = world * 3 * dofs * args.steps / t_total
 
     # roofline of the dominant kernel (the fused residual + RK-stage kernel)
     s_state = 4 if precision == dg.DG_FP32 else 8     # FP64, or the float-float pair of the mixed form
@@ -281,9 +290,10 @@ def run_ours(args, rank, world, device):
 
 
 # ---------------------------------------------------------------------------------------------
-def oracle_sample_rate(workload, nsample, reps=1, seed=11):
+def oracle_sample_rate(workload, nsample, reps=1, seed=11, warmup=0):
     """The FP64 oracle's residual on a seeded sample of the workload's
-    elements, single-threaded: (DOF-updates/s, seconds, sample size)."""
+    elements: (DOF-updates/s averaged over ``reps`` timed evaluations, seconds
+    per evaluation, sample size, per-evaluation rates)."""
     from oracle.dg import Problem
     mesh, field, w = make_workload(workload)
     fs = None
@@ -300,23 +310,32 @@ def oracle_sample_rate(workload, nsample, reps=1, seed=11):
     sub = P.project(field, rule="volume", elems=need)
     U[need] = sub
     P.residual(U, rows[:16])
-    t0 = time.perf_counter()
-    for _ in range(reps):
+    for _ in range(warmup):
         P.residual(U, rows)
-    dt = (time.perf_counter() - t0) / reps
-    return len(rows) * 5 * P.nb / dt, dt, len(rows)
+    rates = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        P.residual(U, rows)
+        rates.append(len(rows) * 5 * P.nb / (time.perf_counter() - t0))
+    dt = len(rows) * 5 * P.nb / float(np.mean(rates))
+    return float(np.mean(rates)), dt, len(rows), rates
 
 
-def cpu_baseline_subprocess(workload, nsample, reps=1):
-    """Run the oracle timing in a child process pinned to one BLAS/OpenMP thread."""
+def _oracle_child(workload, nsample, reps, warmup=0):
+    """Run oracle_sample_rate in a child process pinned to one BLAS/OpenMP thread."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "r = bench.oracle_sample_rate(%r, %d, %d); print(json.dumps(r))" % (ROOT, workload, nsample, reps))
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+            "r = bench.oracle_sample_rate(%r, %d, %d, warmup=%d); print(json.dumps(r))"
+            % (ROOT, workload, nsample, reps, warmup))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
-    rate, sec, n = json.loads(out.stdout.strip().splitlines()[-1])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_subprocess(workload, nsample, reps=1):
+    rate, sec, n, _ = _oracle_child(workload, nsample, reps)
     return {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
             "sample": f"FP64 oracle residual on {n} seeded elements of {workload} (with their neighbours' "
                       f"states), {reps} evaluation(s), {sec:.1f}s each, 1 thread"}
@@ -326,28 +345,21 @@ SAMPLE = {"c1": 1296, "c2": 60000, "c3": 30000, "c4": 60000, "c5": 30000, "c3s":
 
 
 def run_reference(args):
-    """--impl reference: the FP64 oracle on the host cores, each step a bounded sample."""
+    """--impl reference: the FP64 oracle on the host, one thread, each step one
+    residual evaluation of a bounded seeded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     cfg = config_of(args)
     n = max(200, SAMPLE.get(args.workload, 2000) // 3)
-    rates = []
-    for i in range(args.warmup + args.steps):
-        r = cpu_baseline_subprocess(args.workload, n) if i == 0 else None
-        if r is None:
-            rate, _, _ = oracle_sample_rate(args.workload, n, 1, seed=11 + i)
-        else:
-            rate = r["value"]
-        if i >= args.warmup:
-            rates.append(rate)
-    value = float(np.mean(rates))
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
-            "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"FP64 oracle residual on {n} seeded elements of {args.workload} per step"},
-            "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    rate, sec, nrows, rates = _oracle_child(args.workload, n, args.steps, warmup=args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "DOF-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"FP64 oracle residual on {nrows} seeded elements of {args.workload} "
+                                       f"per step, 1 thread"},
+            "e2e": {"value": rate, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
