@@ -57,3 +57,14 @@ def test_workload_configs():
     assert c["tets"] == 6 * 64 ** 3 and c["order"] == 3 and c["dofs"] == 6 * 64 ** 3 * 100
     A.workload = "c5"
     assert bench.config_of(A())["tets"] == 96 * 48 * 48 * 6
+
+
+def test_measured_traffic_scales_with_elements_and_checks_sources(monkeypatch):
+    import bench
+    key = ("mixed", 3, "roe")
+    per_elem, files, _ = bench.MEASURED_TRAFFIC[key]
+    monkeypatch.setitem(bench.MEASURED_TRAFFIC, key, (per_elem, files, bench.kernel_source_hash(files)))
+    assert bench.measured_traffic("f16x2-tc/f32/ff32", 3, "roe", 1000) == pytest.approx(per_elem * 1000)
+    monkeypatch.setitem(bench.MEASURED_TRAFFIC, key, (per_elem, files, "0" * 16))
+    assert bench.measured_traffic("f16x2-tc/f32/ff32", 3, "roe", 1000) is None
+    assert bench.measured_traffic("f32", 2, "rusanov", 1000) is None
