@@ -109,6 +109,12 @@ struct dg_mesh {
     int8_t* d_fperm = nullptr;
     uint16_t* d_tab16 = nullptr;   // f16 operand images of the tables (mixed precision)
     float mix_inv_b1 = 1.f, mix_inv_b2 = 1.f;
+    // mixed precision: faces evaluated once by their owner (lower element index; self-adjacent
+    // faces by the lower local face), traces and face fluxes [ne][4][Nqf][5] FP32
+    int32_t* d_flist = nullptr;    // owned faces e*4+f, ascending
+    int64_t n_flist = 0;
+    float* d_T = nullptr;
+    float* d_H = nullptr;
     void* d_B[3] = {nullptr, nullptr, nullptr};   // state buffers (internal precision)
     void* d_V[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // adjoint work buffers (lazy)
     double* d_io = nullptr;        // FP64 [ne][5][Nb] staging for host copies
