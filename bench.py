@@ -37,14 +37,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "c1": dict(n=6, p=1, jitter=0.10, flux="rusanov", field="vortex", box=False),
-    "c2": dict(n=48, p=2, jitter=0.10, flux="rusanov", field="vortex_noise", box=False),
-    "c3": dict(n=64, p=3, jitter=0.15, flux="roe", field="vortex", box=False),
-    "c4": dict(n=32, p=2, jitter=0.10, flux="rusanov", field="vortex", box=False),
-    "c5": dict(dims=(96, 48, 48), p=3, jitter=0.15, flux="roe", field="pulse", box=True),
+    "c1": dict(n=6, p=1, jitter=0.10, flux="rusanov", field="vortex", box=False, order="morton"),
+    "c2": dict(n=48, p=2, jitter=0.10, flux="rusanov", field="vortex_noise", box=False, order="rcm"),
+    "c3": dict(n=64, p=3, jitter=0.15, flux="roe", field="vortex", box=False, order="morton"),
+    "c4": dict(n=32, p=2, jitter=0.10, flux="rusanov", field="vortex", box=False, order="morton"),
+    "c5": dict(dims=(96, 48, 48), p=3, jitter=0.15, flux="roe", field="pulse", box=True, order="morton"),
     # small case of the c3 kernel for profiler captures (state 157 MB > L2)
-    "c3s": dict(n=32, p=3, jitter=0.15, flux="roe", field="vortex", box=False),
+    "c3s": dict(n=32, p=3, jitter=0.15, flux="roe", field="vortex", box=False, order="morton"),
 }
+ORDER_NAMES = ("morton", "rcm", "asis")
 NB = {1: 4, 2: 10, 3: 20}
 NQ = {1: 4, 2: 14, 3: 24}
 NQF = {1: 3, 2: 6, 3: 12}
@@ -68,6 +69,12 @@ def replica_value(work_per_rank, t_local, world, device=None):
         torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
         t = float(x.item())
     return t, world * work_per_rank / t
+
+
+def order_of(args):
+    """Element order of the run: --order, else the workload's (RCM where the workload names it,
+    a Morton space-filling curve otherwise)."""
+    return args.order or WORKLOADS[args.workload]["order"]
 
 
 def make_workload(name):
@@ -216,8 +223,9 @@ def run_ours(args, rank, world, device):
         from paper_2209_01877_gb300 import inputs as I
         fs = tuple(I.freestream_state(0.3))
     t0 = time.time()
+    ren = {"morton": dg.DG_ORDER_MORTON, "rcm": dg.DG_ORDER_RCM, "asis": dg.DG_ORDER_ASIS}[order_of(args)]
     M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, None if not w["box"] else mesh.bc_tag, order=p, precision=precision,
-                flux=dg.DG_ROE if flux == "roe" else dg.DG_RUSANOV, renumber=dg.DG_ORDER_RCM, freestream=fs)
+                flux=dg.DG_ROE if flux == "roe" else dg.DG_RUSANOV, renumber=ren, freestream=fs)
     U0 = M.project(field)
     if w["field"] == "vortex_noise":
         from paper_2209_01877_gb300 import inputs as I
@@ -290,7 +298,7 @@ def run_ours(args, rank, world, device):
                 "kernel": "k_residual<double,P,FLUX,RK>", "algorithmic_bytes_per_launch": bytes_per_launch,
                 "algorithmic_flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms}
     else:
-        kname = "k_residual<float,P,FLUX,RK>" if precision == dg.DG_FP32 else "k_residual_mixed<P,FLUX>"
+        kname = "k_residual<float,P,FLUX,RK>" if precision == dg.DG_FP32 else "k_stage_mixed<P,FLUX>"
         roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": hbm_achieved / peaks["hbm_gbs"], "traffic": None,
                 "peak_source": f"hbm_gbs of {peak_src} peaks", "kernel": kname,
@@ -406,8 +414,9 @@ def config_of(args):
     ne = 6 * (w["n"] ** 3 if not w["box"] else int(np.prod(w["dims"])))
     desc = {"c1": "6^3x6 periodic cube", "c2": "48^3x6 periodic cube", "c3": "64^3x6 periodic cube",
             "c4": "32^3x6 periodic cube", "c5": "96x48x48x6 box channel", "c3s": "32^3x6 periodic cube"}
+    oname = {"morton": "Morton order", "rcm": "RCM order", "asis": "input (random) order"}[order_of(args)]
     return {"workload": f"{args.workload}: {desc[args.workload]}, P{w['p']}, {ne} tets, {w['flux']} flux, "
-                        f"jitter {w['jitter']}, RCM order, field {w['field']}",
+                        f"jitter {w['jitter']}, {oname}, field {w['field']}",
             "tets": ne, "order": w["p"], "flux": w["flux"], "dofs": ne * 5 * I.n_basis(w["p"]),
             "step": "one SSP-RK3 step = 3 fused residual+stage launches",
             "l2": "inputs larger than L2 (state >= 157 MB vs 129 MB L2)" if w["p"] >= 2 and ne > 100000
@@ -544,6 +553,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64", "fp32"])
+    ap.add_argument("--order", default=None, choices=ORDER_NAMES,
+                    help="element order (default: the workload's; RCM for c2, Morton otherwise)")
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 comparison leg of a mixed run")
     ap.add_argument("--study", choices=["temporal-mp", "renumbering", "adjoint", "aux"], default=None,
                     help="print a study table instead of the benchmark line")

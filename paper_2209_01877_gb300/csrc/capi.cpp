@@ -50,9 +50,9 @@ void free_mesh(dg_mesh* m) {
     cudaFree(m->d_tab64);
     cudaFree(m->d_fperm);
     cudaFree(m->d_tab16);
-    cudaFree(m->d_flist);
-    cudaFree(m->d_T);
-    cudaFree(m->d_H);
+    cudaFree(m->d_mslot);
+    cudaFree(m->d_mlist);
+    cudaFree(m->d_mcnt);
     for (auto& b : m->d_B) cudaFree(b);
     for (auto& b : m->d_V) cudaFree(b);
     cudaFree(m->d_io);
@@ -149,20 +149,13 @@ dg_status dg_mesh_create(const int32_t* tet_vid, const double* tet_xyz, const in
         std::vector<uint16_t> t16;
         dg::build_mixed_tables(m->p, m->ref, t16, m->mix_inv_b1, m->mix_inv_b2);
         DG_TRY(upload(&m->d_tab16, t16.data(), t16.size(), s));
-        std::vector<int32_t> owned;
-        owned.reserve((size_t)ne * 2 + m->host.n_bfaces);
-        for (int64_t e = 0; e < ne; ++e)
-            for (int f = 0; f < 4; ++f) {
-                const int32_t n = m->host.nbr[e * 4 + f];
-                const int fn = m->host.fcode[e * 4 + f] & 3;
-                if (n < 0 || n > e || (n == e && f < fn)) owned.push_back((int32_t)(e * 4 + f));
-            }
-        m->n_flist = (int64_t)owned.size();
-        DG_TRY(upload(&m->d_flist, owned.data(), owned.size(), s));
-        const size_t nt = (size_t)ne * 4 * m->nqf * 5;
-        cudaError_t e1 = cudaMalloc(reinterpret_cast<void**>(&m->d_T), nt * sizeof(float) + 256);
-        if (e1 == cudaSuccess) e1 = cudaMalloc(reinterpret_cast<void**>(&m->d_H), nt * sizeof(float) + 256);
-        if (e1 != cudaSuccess) { free_mesh(m); return cuda_fail(e1, "cudaMalloc(traces)"); }
+        std::vector<uint32_t> slot;
+        std::vector<uint8_t> lists;
+        std::vector<int32_t> cnt;
+        dg::build_mixed_tiles(m->host, slot, lists, cnt);
+        DG_TRY(upload(&m->d_mslot, slot.data(), slot.size(), s));
+        DG_TRY(upload(&m->d_mlist, lists.data(), lists.size(), s));
+        DG_TRY(upload(&m->d_mcnt, cnt.data(), cnt.size(), s));
     }
     if (m->precision == DG_FP64) {
         m->d_tab = m->d_tab64;   // shared; freed once below

@@ -109,12 +109,11 @@ struct dg_mesh {
     int8_t* d_fperm = nullptr;
     uint16_t* d_tab16 = nullptr;   // f16 operand images of the tables (mixed precision)
     float mix_inv_b1 = 1.f, mix_inv_b2 = 1.f;
-    // mixed precision: faces evaluated once by their owner (lower element index; self-adjacent
-    // faces by the lower local face), traces and face fluxes [ne][4][Nqf][5] FP32
-    int32_t* d_flist = nullptr;    // owned faces e*4+f, ascending
-    int64_t n_flist = 0;
-    float* d_T = nullptr;
-    float* d_H = nullptr;
+    // mixed precision: per tile of consecutive elements, the slot codes, the cross and work
+    // lists and their counts (build_mixed_tiles)
+    uint32_t* d_mslot = nullptr;
+    uint8_t* d_mlist = nullptr;
+    int32_t* d_mcnt = nullptr;
     void* d_B[3] = {nullptr, nullptr, nullptr};   // state buffers (internal precision)
     void* d_V[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // adjoint work buffers (lazy)
     double* d_io = nullptr;        // FP64 [ne][5][Nb] staging for host copies
@@ -143,6 +142,8 @@ cudaError_t launch_residual_mixed(dg_mesh* m, const float* U_hi, const float* U_
                                   const float* U0_lo, float* out_hi, float* out_lo, int mode, double dt, double a,
                                   double b, cudaStream_t s);
 void build_mixed_tables(int p, const RefData& ref, std::vector<uint16_t>& out, float& inv_b1, float& inv_b2);
+void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vector<uint8_t>& lists,
+                       std::vector<int32_t>& cnt);
 dg_status set_error(dg_status code, const char* msg);   // sets dg_last_error() for the calling thread
 int mixed_tab_halves(int p);
 }  // namespace dg

@@ -28,33 +28,54 @@ pytestmark = pytest.mark.gpu
 TOLMIX = 5e-6
 
 
-def _mesh(m, p, flux, precision=dg.DG_MIXED_FP16, fs=None):
+# element orders: a space-filling curve puts most faces inside one 24-element tile (evaluated
+# once, flux written to both sides); reverse Cuthill-McKee puts none there (every face takes the
+# neighbour-trace path)
+ORDERS = {"morton": dg.DG_ORDER_MORTON, "rcm": dg.DG_ORDER_RCM}
+
+
+def _mesh(m, p, flux, precision=dg.DG_MIXED_FP16, fs=None, order="morton"):
     tag = None if all(m.periodic) else m.bc_tag
     return dg.Mesh(m.tet_vid, m.tet_xyz, tag, order=p, precision=precision,
-                   flux=dg.DG_ROE if flux == "roe" else dg.DG_RUSANOV, renumber=dg.DG_ORDER_RCM,
+                   flux=dg.DG_ROE if flux == "roe" else dg.DG_RUSANOV, renumber=ORDERS[order],
                    freestream=tuple(fs) if fs is not None else (0, 0, 0, 0, 0))
 
 
+@pytest.mark.parametrize("order", ["morton", "rcm"])
 @pytest.mark.parametrize("p", [1, 2, 3])
 @pytest.mark.parametrize("flux", ["rusanov", "roe"])
-def test_mixed_residual_periodic(p, flux):
+def test_mixed_residual_periodic(p, flux, order):
     m = I.make_periodic_cube(4, jitter=0.15)
     P = Problem(m.tet_vid, m.tet_xyz, None, p=p, flux=flux)
     U = vortex_state(P, radius=0.15)
     R = P.residual(U)
-    Rg = gpu_residual(_mesh(m, p, flux), U)
+    Rg = gpu_residual(_mesh(m, p, flux, order=order), U)
     assert max_rel_err(Rg, R, term_scale=residual_term_scale(P, U)) < TOLMIX
 
 
+@pytest.mark.parametrize("order", ["morton", "rcm"])
 @pytest.mark.parametrize("p", [1, 2, 3])
-def test_mixed_residual_box(p):
+def test_mixed_residual_box(p, order):
     m = I.make_box_channel(4, 3, 3, lengths=(2.0, 1.0, 1.0), jitter=0.15)
     fs = I.freestream_state(0.3)
     P = Problem(m.tet_vid, m.tet_xyz, m.bc_tag, p=p, flux="roe", freestream=fs)
     U = P.project(lambda x: I.gaussian_pulse(x, (0.9, 0.5, 0.5), width=0.3))
     R = P.residual(U)
-    Rg = gpu_residual(_mesh(m, p, "roe", fs=fs), U)
+    Rg = gpu_residual(_mesh(m, p, "roe", fs=fs, order=order), U)
     assert max_rel_err(Rg, R, term_scale=residual_term_scale(P, U)) < TOLMIX
+
+
+@pytest.mark.parametrize("order", ["morton", "rcm", "asis"])
+def test_mixed_residual_orders_agree(order):
+    """Every element order gives the same residual up to FP32 round-off, whichever faces
+    land inside a tile."""
+    m = I.make_periodic_cube(5, jitter=0.15)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=3, flux="roe")
+    U = vortex_state(P, radius=0.2)
+    ren = {"morton": dg.DG_ORDER_MORTON, "rcm": dg.DG_ORDER_RCM, "asis": dg.DG_ORDER_ASIS}[order]
+    M = dg.Mesh(m.tet_vid, m.tet_xyz, None, order=3, precision=dg.DG_MIXED_FP16, flux=dg.DG_ROE, renumber=ren)
+    Rg = gpu_residual(M, U)
+    assert max_rel_err(Rg, P.residual(U), term_scale=residual_term_scale(P, U)) < TOLMIX
 
 
 def test_mixed_ragged_tile_and_free_stream():
@@ -64,8 +85,9 @@ def test_mixed_ragged_tile_and_free_stream():
     assert m.ne % 24 != 0
     P = Problem(m.tet_vid, m.tet_xyz, None, p=3, flux="roe")
     U = vortex_state(P, radius=0.2)
-    Rg = gpu_residual(_mesh(m, 3, "roe"), U)
-    assert max_rel_err(Rg, P.residual(U), term_scale=residual_term_scale(P, U)) < TOLMIX
+    for order in ORDERS:
+        Rg = gpu_residual(_mesh(m, 3, "roe", order=order), U)
+        assert max_rel_err(Rg, P.residual(U), term_scale=residual_term_scale(P, U)) < TOLMIX
     Uf = P.project(I.uniform_flow)
     Rf = gpu_residual(_mesh(m, 3, "roe"), Uf)
     assert np.abs(Rf).max() < 1e-5 * max(residual_term_scale(P, Uf))
