@@ -74,7 +74,7 @@ def replica_value(work_per_rank, t_local, world, device=None):
 def order_of(args):
     """Element order of the run: --order, else the workload's (RCM where the workload names it,
     a Morton space-filling curve otherwise)."""
-    return args.order or WORKLOADS[args.workload]["order"]
+    return getattr(args, "order", None) or WORKLOADS[args.workload]["order"]
 
 
 def make_workload(name):

@@ -52,7 +52,8 @@ void free_mesh(dg_mesh* m) {
     cudaFree(m->d_tab16);
     cudaFree(m->d_mslot);
     cudaFree(m->d_mlist);
-    cudaFree(m->d_mcnt);
+    cudaFree(m->d_mhdr);
+    cudaFree(m->d_mxnbr);
     for (auto& b : m->d_B) cudaFree(b);
     for (auto& b : m->d_V) cudaFree(b);
     cudaFree(m->d_io);
@@ -151,11 +152,12 @@ dg_status dg_mesh_create(const int32_t* tet_vid, const double* tet_xyz, const in
         DG_TRY(upload(&m->d_tab16, t16.data(), t16.size(), s));
         std::vector<uint32_t> slot;
         std::vector<uint8_t> lists;
-        std::vector<int32_t> cnt;
-        dg::build_mixed_tiles(m->host, slot, lists, cnt);
+        std::vector<int32_t> cnt, xnbr;
+        dg::build_mixed_tiles(m->host, slot, lists, cnt, xnbr);
         DG_TRY(upload(&m->d_mslot, slot.data(), slot.size(), s));
         DG_TRY(upload(&m->d_mlist, lists.data(), lists.size(), s));
-        DG_TRY(upload(&m->d_mcnt, cnt.data(), cnt.size(), s));
+        DG_TRY(upload(&m->d_mhdr, cnt.data(), cnt.size(), s));
+        DG_TRY(upload(&m->d_mxnbr, xnbr.data(), xnbr.size(), s));
     }
     if (m->precision == DG_FP64) {
         m->d_tab = m->d_tab64;   // shared; freed once below

@@ -110,10 +110,11 @@ struct dg_mesh {
     uint16_t* d_tab16 = nullptr;   // f16 operand images of the tables (mixed precision)
     float mix_inv_b1 = 1.f, mix_inv_b2 = 1.f;
     // mixed precision: per tile of consecutive elements, the slot codes, the cross and work
-    // lists and their counts (build_mixed_tiles)
+    // lists and the tile headers (build_mixed_tiles)
     uint32_t* d_mslot = nullptr;
     uint8_t* d_mlist = nullptr;
-    int32_t* d_mcnt = nullptr;
+    int32_t* d_mhdr = nullptr;
+    int32_t* d_mxnbr = nullptr;
     void* d_B[3] = {nullptr, nullptr, nullptr};   // state buffers (internal precision)
     void* d_V[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // adjoint work buffers (lazy)
     double* d_io = nullptr;        // FP64 [ne][5][Nb] staging for host copies
@@ -143,7 +144,7 @@ cudaError_t launch_residual_mixed(dg_mesh* m, const float* U_hi, const float* U_
                                   double b, cudaStream_t s);
 void build_mixed_tables(int p, const RefData& ref, std::vector<uint16_t>& out, float& inv_b1, float& inv_b2);
 void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vector<uint8_t>& lists,
-                       std::vector<int32_t>& cnt);
+                       std::vector<int32_t>& hdr, std::vector<int32_t>& xnbr);
 dg_status set_error(dg_status code, const char* msg);   // sets dg_last_error() for the calling thread
 int mixed_tab_halves(int p);
 }  // namespace dg

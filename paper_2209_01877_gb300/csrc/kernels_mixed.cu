@@ -19,28 +19,32 @@
 //     b dt R is formed in FP32 -- it is small against U, so its rounding sits
 //     far below the FP32 residual's own.
 //
-// One persistent CTA per SM (512 threads, 512 TMEM columns) walks over tiles
-// of ET = 24 consecutive elements (5 ET = 120 rows of a 128-row MMA).  A face
-// whose two elements lie in the same tile is evaluated once (by the lower
-// slot): both traces come from the tile's own MMA and the flux is written to
-// both sides.  Only faces to other tiles read the neighbour's coefficients
-// (from L2: consecutive elements of a space-filling-curve or RCM order are
-// spatial neighbours) for a trace MMA of their own.  Per tile:
+// One persistent CTA per SM (512 threads, 512 TMEM columns) runs two
+// independent pipelines ("contexts" of 256 threads, 256 TMEM columns and their
+// own shared-memory buffers; the basis tables are shared).  While one context
+// waits on the tensor cores or on memory, the other computes.  A context walks
+// over tiles of ET = 12 consecutive elements (5 ET = 60 rows of a 64-row MMA;
+// an M = 64 accumulator occupies TMEM lanes 0-15 of each 32-lane quarter).  A
+// face whose two elements lie in the same tile is evaluated once (by the
+// lower slot): both traces come from the tile's own MMA and the flux is
+// written to both sides.  Only faces to other tiles read the neighbour's
+// coefficients (from L2: consecutive elements of a space-filling-curve or RCM
+// order are spatial neighbours) for a trace MMA of their own.  Per tile:
 //   build    operand rows: own coefficients (modes 1..), neighbours in other
-//            tiles; per-face geometry and mean-state fluxes; per-element
-//            scaled J^-1 and mean contravariant flux;
+//            tiles; per-element scaled J^-1 and mean-state fluxes;
 //   MMA 1    own values at the 4 Nqf face points and the Nq volume points,
-//            and the cross-tile neighbours' traces (all 4 of their faces; the
-//            matching face is picked when staging);
+//            and the cross-tile neighbours' traces (blocks of one neighbour
+//            face: a 16-row slice of the face-point table); meanwhile the
+//            per-face normals and mean-state normal fluxes;
 //   stage    TMEM -> shared memory (FP32 point states);
 //   flux     volume points: contravariant flux deviation; face points:
 //            Rusanov / Roe flux (ghost state on boundary faces) written to
 //            the owner's and, for in-tile faces, the partner's operand;
 //   MMA 2    projection onto the weighted basis gradients and face lift;
 //   epilogue R, or the RK stage in float-float, straight to global memory.
-// Every wait on the tensor cores is bounded; on time-out the kernel sets a
-// status bit and leaves the tile loop (all threads together), then frees its
-// tensor memory.
+// Every wait on the tensor cores is bounded; on time-out the context sets a
+// status bit and leaves its tile loop (all its threads together); the CTA
+// frees its tensor memory when both contexts are done.
 #include <algorithm>
 #include <cstring>
 
@@ -55,18 +59,16 @@ namespace dg {
 namespace {
 
 constexpr int MT = 512;      // threads per CTA
-constexpr int ET = 24;       // elements per tile
+constexpr int CT = 256;      // threads per context
+constexpr int ET = 12;       // elements per tile
 constexpr int SLOTS = 4 * ET;
-constexpr int PB = 24;       // cross-tile face pairs per neighbour operand block (120 rows)
-constexpr int MAXBLK = 4;    // blocks: every face of the tile may cross
-constexpr int TMEM_COLS = 512;
+constexpr int PB = 12;       // cross-tile face pairs per neighbour operand block (60 rows)
+constexpr int TMEM_COLS = 512, CTX_COLS = 256;
 constexpr long WAIT_ITERS = 20000000;
 
+constexpr int r8(int x) { return (x + 7) / 8 * 8; }
 constexpr int r16(int x) { return (x + 15) / 16 * 16; }
 constexpr int a128(int x) { return (x + 127) / 128 * 128; }
-// smallest s >= n with s = 5 (mod 32): element stride of the point-state staging, so that the
-// 32 lanes of a TMEM row read (rows 5e + v) store to 32 distinct banks
-constexpr int ustride(int n) { return n + ((5 - n) % 32 + 32) % 32; }
 
 }  // namespace
 
@@ -76,45 +78,69 @@ constexpr int ustride(int n) { return n + ((5 - n) % 32 + 32) % 32; }
 //   bits 2-8   partner slot (in-tile faces)
 //   bits 9-11  relative orientation (face-point permutation index)
 //   bits 12-18 cross index (faces to other tiles)
-//   bits 19-20 neighbour's local face (faces to other tiles)
 //   bits 21-22 boundary type
+// Tile header (THDR ints): cross count, work count, number of neighbour blocks, then one word per
+// block: the neighbours' common local face (bits 0-1), first operand row (bits 2-11, a multiple
+// of 8), face pairs (bits 12-16), first cross index (bits 17-23).  Faces to other tiles are
+// ordered by the neighbour's local face, so that every block of neighbour rows multiplies one
+// 16-row slice of the face-point table.  Per cross index, the neighbour's element id.
 enum { SK_OWN = 0, SK_SKIP = 1, SK_CROSS = 2, SK_BND = 3 };
+constexpr int THDR = 12;
+constexpr int MAXB = 7;       // neighbour blocks: sum over the 4 faces of ceil(pairs / PB) <= 4 + 3
+constexpr int ANR = 288;      // neighbour operand rows: 48 pairs x 5 + 8-row alignment of 7 blocks
 
 template <int P>
 struct SPlan {
-    static constexpr int NB = nb_of(P), NQ = nq_of(P), NQF = nqf_of(P), NF = 4 * NQF, NPT = NF + NQ;
-    static constexpr int NQ4 = (NQ + 3) / 4 * 4;
+    static constexpr int NB = nb_of(P), NQ = nq_of(P), NQF = nqf_of(P), NF = 4 * NQF;
+    static constexpr int NQ4 = (NQ + 3) / 4 * 4, NQF4 = (NQF + 3) / 4 * 4;
+    // own-point table rows / D1 columns: face f point q at FPAD f + q, volume point q at 4 FPAD + q
+    static constexpr int FPAD = NQF <= 8 ? 8 : 16;
+    static constexpr int NPT = 4 * FPAD + NQ;
     // operands hold interleaved split pairs: logical index k -> positions 2k (hi), 2k+1 (lo)
     static constexpr int K1 = r16(2 * NB);        // modes
-    static constexpr int N1 = r16(NPT);           // own points: face points f*Nqf+q, then volume points
-    static constexpr int NN = r16(NF);            // neighbour traces: the face-point rows of the same table
+    static constexpr int N1 = r8(NPT);            // M = 64 MMAs take N in steps of 8
+    static constexpr int NN = 16;                 // neighbour traces: a 16-row slice of the same table
     static constexpr int KL2 = 3 * NQ + NF;       // logical (k, q) then (f, q)
     static constexpr int K2 = r16(2 * KL2);
-    static constexpr int N2 = r16(NB);
+    static constexpr int N2 = r8(NB);
     static constexpr int NCH = (NB + 3) / 4;      // 4-mode chunks
-    // f16 table images in global memory (halves): TB1 a|b, TB2 a|b
+    // f16 table images in global memory (halves): T1 a|b, T2 a|b
     static constexpr int G_T1 = 0, G_T2 = 2 * N1 * K1, TAB_HALVES = G_T2 + 2 * N2 * K2;
-    // tensor memory: D1 (own points), DN[4] (neighbour traces), D2[2] (projection over two K halves)
-    static constexpr int C_D1 = 0, C_DN = N1, C_D2 = C_DN + MAXBLK * NN;
-    static_assert(C_D2 + 2 * N2 <= TMEM_COLS, "tensor memory");
-    static constexpr int USTR = ustride(5 * NPT);
-    // shared memory (bytes)
+    // tensor memory of a context: D1 (own points), DN[MAXB] (neighbour traces), D2[2] (projection,
+    // two K halves)
+    static constexpr int C_D1 = 0, C_DN = r16(N1), C_D2 = C_DN + MAXB * NN;
+    static_assert(C_D2 + 2 * N2 <= CTX_COLS, "tensor memory");
+    static_assert(3 * FPAD + NN <= N1 + 8, "neighbour slice inside table 1");
+    // point-state staging [ET][5][VSTR]: VSTR = 4 (mod 8) and >= the staged columns, so that the
+    // 16-byte stores of 8 consecutive rows (5e + v) and the volume-point loads avoid bank conflicts
+    static constexpr int SCOLS = (NPT + 7) / 8 * 8;
+    static constexpr int VSTR = SCOLS + ((4 - SCOLS % 8) + 8) % 8;
+    static constexpr int USTR = 5 * VSTR;
+    static constexpr int ELW = 52;                // per element: I[9], Is[9], Gbar_s[15], Fbar[15], ts, inv2
+    // shared memory (bytes): tables, then one region per context
     static constexpr int SZ_T1 = 2 * N1 * K1 * 2, SZ_T2 = 2 * N2 * K2 * 2;
-    static constexpr int SZ_A1 = 128 * K1 * 2, SZ_AN = MAXBLK * SZ_A1, SZ_A2 = 128 * K2 * 2;
+    static constexpr int SZ_A1 = 64 * K1 * 2, SZ_AN = ANR * K1 * 2, SZ_A2 = 64 * K2 * 2;
     static constexpr int SZ_AU = (SZ_A1 + SZ_AN) > SZ_A2 ? (SZ_A1 + SZ_AN) : SZ_A2;
-    static constexpr int O_T1 = 0, O_T2 = a128(O_T1 + SZ_T1), O_AU = a128(O_T2 + SZ_T2);
-    static constexpr int O_SU = a128(O_AU + SZ_AU);                        // float [ET][USTR]
-    static constexpr int O_SN = a128(O_SU + ET * USTR * 4);                // float [SLOTS][NQF][5]
-    static constexpr int O_ROW = a128(O_SN + SLOTS * NQF * 5 * 4);        // float2 [128 + MAXBLK*128] (mean, 1/scale)
-    static constexpr int O_GEO = a128(O_ROW + (128 + MAXBLK * 128) * 8);  // float4 [SLOTS] (n, sc)
-    static constexpr int O_FBN = a128(O_GEO + SLOTS * 16);                // float [SLOTS][5]
-    static constexpr int O_EL = a128(O_FBN + SLOTS * 5 * 4);              // float [ET][28]: I_s, Gbar_s, 1/ts
-    static constexpr int O_CODE = a128(O_EL + ET * 28 * 4);               // uint32 [SLOTS]
-    static constexpr int O_LIST = O_CODE + SLOTS * 4;                      // uint8 [2*SLOTS]: cross, work
-    static constexpr int O_PERM = O_LIST + 2 * SLOTS;                      // int8 [6][NQF]
-    static constexpr int O_MB = a128(O_PERM + 6 * NQF);                    // mbarrier, tmem slot
-    static constexpr int BYTES = O_MB + 16;
+    static constexpr int O_T1 = 0, O_T2 = a128(O_T1 + SZ_T1), O_CTX = a128(O_T2 + SZ_T2);
+    // context-relative offsets
+    static constexpr int X_AU = 0;
+    static constexpr int X_SU = a128(X_AU + SZ_AU);                        // float [ET][5][VSTR]
+    static constexpr int X_SN = a128(X_SU + ET * USTR * 4);                // float [SLOTS][5][NQF4]
+    static constexpr int X_ROW = a128(X_SN + SLOTS * 5 * NQF4 * 4);       // float2 [64 + ANR] (mean, factor)
+    static constexpr int X_GEO = a128(X_ROW + (64 + ANR) * 8);            // float4 [SLOTS] (n, sc)
+    static constexpr int X_FBN = a128(X_GEO + SLOTS * 16);                // float [SLOTS][5]
+    static constexpr int X_EL = a128(X_FBN + SLOTS * 5 * 4);              // float [ET][ELW]
+    static constexpr int X_HDR = a128(X_EL + ET * ELW * 4);               // int [THDR]
+    static constexpr int X_CODE = X_HDR + THDR * 4;                        // uint32 [SLOTS]
+    static constexpr int X_LIST = X_CODE + SLOTS * 4;                      // uint8 [2*SLOTS]: cross, work
+    static constexpr int X_MB = a128(X_LIST + 2 * SLOTS);                  // mbarrier
+    static constexpr int CTX_BYTES = a128(X_MB + 16);
+    static constexpr int O_PERM = O_CTX + 2 * CTX_BYTES;                   // int8 [6][NQF]
+    static constexpr int O_SLOT = a128(O_PERM + 6 * NQF);                  // tmem slot
+    static constexpr int BYTES = O_SLOT + 16;
     static_assert(BYTES <= 227 * 1024, "shared memory");
+    // the last neighbour block's MMA reads up to 63 rows past its own: inside the context's staging
+    static_assert(SZ_A1 + (ANR + 64) * K1 * 2 <= X_SN, "neighbour operand overrun");
 };
 
 struct StageArgs {
@@ -125,10 +151,10 @@ struct StageArgs {
     float* out_hi;          // RK: new state planes; residual mode: R (FP32)
     float* out_lo;
     const float* jinv;      // [ne][9] FP32
-    const int32_t* nbr;     // [ne][4]
     const uint32_t* slot;   // [ntiles][SLOTS] slot codes
     const uint8_t* tlist;   // [ntiles][2*SLOTS] cross list, work list
-    const int32_t* tcnt;    // [ntiles][2] cross count, work count
+    const int32_t* thdr;    // [ntiles][THDR] tile header
+    const int32_t* xnbr;    // [ntiles][SLOTS] neighbour element of each cross index
     const int8_t* fperm;    // [6][Nqf]
     const uint16_t* tab16;  // f16 table images
     int64_t ne;
@@ -141,20 +167,18 @@ struct StageArgs {
 };
 
 namespace {
-
-// power of two 2^k with 2^k * x in [8, 16) (x > 0); 1 for x <= 0 or non-finite
+// power of two 2^k with 2^k * x in [8, 16) for normal x > 0 (from the exponent field); 1 for
+// x <= 0, subnormal, huge or non-finite x
 __device__ __forceinline__ float pow2_scale(float x) {
-    if (!(x > 0.f) || !(x < 3.0e38f)) return 1.f;
-    int e;
-    frexpf(x, &e);   // x = m 2^e, m in [0.5, 1)
-    return ldexpf(1.f, 4 - e);
+    const int eb = (__float_as_int(x) >> 23) & 0xff;   // x in [2^(eb-127), 2^(eb-126))
+    return (x > 0.f && eb >= 3 && eb < 255) ? __int_as_float((257 - eb) << 23) : 1.f;
 }
 
 // (hi, lo) f16 pair of x packed in one 32-bit word (hi in the low half = even K position)
 __device__ __forceinline__ uint32_t split_pair(float x) {
-    const __half hi = __float2half_rn(x);
-    const __half lo = __float2half_rn(x - __half2float(hi));
-    return (uint32_t)__half_as_ushort(hi) | ((uint32_t)__half_as_ushort(lo) << 16);
+    const float hi = __half2float(__float2half_rn(x));
+    const __half2 w = __floats2half2_rn(x, x - hi);
+    return *reinterpret_cast<const uint32_t*>(&w);
 }
 
 // grad_x lambda_f (row f-1 of J^-1; lambda_0 = 1 - sum of the others)
@@ -176,23 +200,23 @@ __device__ __forceinline__ float elem_flux_scale(const float ub[5], const float*
     float mag = 0.f;
 #pragma unroll
     for (int v = 0; v < 5; ++v) mag += fabsf(ub[v]);
-    const float ri = 1.f / ub[0];
+    const float ri = __fdividef(1.f, ub[0]);
     const float vel0 = ub[1] * ri, vel1 = ub[2] * ri, vel2 = ub[3] * ri;
     const float pr = (gamma - 1.f) * (ub[4] - 0.5f * (ub[1] * vel0 + ub[2] * vel1 + ub[3] * vel2));
     const float spd = sqrtf(vel0 * vel0 + vel1 * vel1 + vel2 * vel2) + sqrtf(fabsf(gamma * pr * ri));
-    float ih = 0.f;
+    float ih2 = 0.f;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         float g0, g1, g2;
         grad_lambda(I, f, g0, g1, g2);
-        ih = fmaxf(ih, sqrtf(g0 * g0 + g1 * g1 + g2 * g2));
+        ih2 = fmaxf(ih2, g0 * g0 + g1 * g1 + g2 * g2);
     }
-    return pow2_scale(mag * spd * ih);
+    return pow2_scale(mag * spd * sqrtf(ih2));
 }
 
-// physical flux F_d (d = 0..2) of state U with velocity and pressure
+// physical flux F_d (d = 0..2) of state U
 __device__ __forceinline__ void euler_fluxes(const float U[5], float gamma, float F[3][5]) {
-    const float ri = 1.f / U[0];
+    const float ri = __fdividef(1.f, U[0]);
     const float vel[3] = {U[1] * ri, U[2] * ri, U[3] * ri};
     const float p = (gamma - 1.f) * (U[4] - 0.5f * (U[1] * vel[0] + U[2] * vel[1] + U[3] * vel[2]));
 #pragma unroll
@@ -223,22 +247,104 @@ __device__ __forceinline__ void contravariant(const float U[5], const float* Is,
     }
 }
 
-__device__ __forceinline__ bool phys_ok(const float U[5], float gamma) {
-    const float p = (gamma - 1.f) * (U[4] - 0.5f * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0]);
-    return U[0] > 0.f && p > 0.f;
+// positive density and pressure: rho > 0 and 2 rho E > |m|^2 (false for NaN)
+__device__ __forceinline__ bool phys_ok(const float U[5]) {
+    return U[0] > 0.f && 2.f * U[0] * U[4] > U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
 }
 
-// one thread polls the mbarrier; the others wait at the block barrier; false (for every
-// thread) if the wait gave up
-__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t& phase) {
-    const bool ok = threadIdx.x == 0 ? tc::mbar_wait(mbar, phase, WAIT_ITERS) : true;
-    phase ^= 1u;
-    return !__syncthreads_or(!ok);
+// ---- FP32 numerical fluxes for the mixed path ---------------------------------------------------
+// The formulas of rusanov_flux / roe_flux (Rusanov: Eq. 11's face flux with the larger of the two
+// sides' |u.n| + c; Roe 1981 with Roe-averaged velocity, enthalpy and sound speed, acoustic,
+// entropy and shear waves, optional Harten fix), evaluated with the hardware reciprocal and
+// reciprocal square root (relative error ~1e-7, the level of the rest of the FP32 flux path).
+// Both return false if either state has non-positive density or pressure (or is not finite).
+struct Prim {
+    float ri, u0, u1, u2, p, un;
+};
+__device__ __forceinline__ Prim prim_of(const float U[5], const float n[3], float g1) {
+    Prim w;
+    w.ri = __fdividef(1.f, U[0]);
+    w.u0 = U[1] * w.ri;
+    w.u1 = U[2] * w.ri;
+    w.u2 = U[3] * w.ri;
+    w.p = g1 * (U[4] - 0.5f * (U[1] * w.u0 + U[2] * w.u1 + U[3] * w.u2));
+    w.un = w.u0 * n[0] + w.u1 * n[1] + w.u2 * n[2];
+    return w;
+}
+__device__ __forceinline__ bool prim_ok(const float U[5], const Prim& w) { return U[0] > 0.f && w.p > 0.f; }
+
+// half the sum of the two sides' normal fluxes, 1/2 (F(UL) + F(UR)).n
+__device__ __forceinline__ void mean_normal_flux(const float UL[5], const float UR[5], const Prim& L, const Prim& R,
+                                                 const float n[3], float F[5]) {
+    const float ps = L.p + R.p;
+    F[0] = 0.5f * (UL[0] * L.un + UR[0] * R.un);
+    F[1] = 0.5f * fmaf(ps, n[0], UL[1] * L.un + UR[1] * R.un);
+    F[2] = 0.5f * fmaf(ps, n[1], UL[2] * L.un + UR[2] * R.un);
+    F[3] = 0.5f * fmaf(ps, n[2], UL[3] * L.un + UR[3] * R.un);
+    F[4] = 0.5f * ((UL[4] + L.p) * L.un + (UR[4] + R.p) * R.un);
 }
 
-// split-f16 operand row from 20 (Nb) FP32 coefficients: modes 1.. scaled by a power of two that
-// brings their largest magnitude into [8, 16); returns (mean = sqrt6 c_0, inv_beta1 / scale), the
-// factors that turn the row's MMA result (against the beta1-scaled table) into point values
+__device__ __forceinline__ bool rusanov_f32(const float UL[5], const float UR[5], const float n[3], float gamma,
+                                            float H[5]) {
+    const float g1 = gamma - 1.f;
+    const Prim L = prim_of(UL, n, g1), R = prim_of(UR, n, g1);
+    float F[5];
+    mean_normal_flux(UL, UR, L, R, n, F);
+    const float c2L = gamma * L.p * L.ri, c2R = gamma * R.p * R.ri;
+    const float sL = fabsf(L.un) + c2L * rsqrtf(c2L), sR = fabsf(R.un) + c2R * rsqrtf(c2R);
+    const float hs = 0.5f * fmaxf(sL, sR);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) H[v] = fmaf(-hs, UR[v] - UL[v], F[v]);
+    return prim_ok(UL, L) && prim_ok(UR, R);
+}
+
+__device__ __forceinline__ bool roe_f32(const float UL[5], const float UR[5], const float n[3], float gamma, float eps,
+                                        float H[5]) {
+    const float g1 = gamma - 1.f;
+    const Prim L = prim_of(UL, n, g1), R = prim_of(UR, n, g1);
+    float F[5];
+    mean_normal_flux(UL, UR, L, R, n, F);
+    const float sqL = UL[0] * rsqrtf(UL[0]), sqR = UR[0] * rsqrtf(UR[0]);
+    const float wden = __fdividef(1.f, sqL + sqR);
+    const float wL = sqL * wden, wR = sqR * wden;
+    const float uh0 = fmaf(wL, L.u0, wR * R.u0), uh1 = fmaf(wL, L.u1, wR * R.u1), uh2 = fmaf(wL, L.u2, wR * R.u2);
+    const float HL = (UL[4] + L.p) * L.ri, HR = (UR[4] + R.p) * R.ri;
+    const float Hh = fmaf(wL, HL, wR * HR);
+    const float q2 = 0.5f * (uh0 * uh0 + uh1 * uh1 + uh2 * uh2);
+    const float c2 = g1 * (Hh - q2);
+    const float ich = rsqrtf(c2);
+    const float ch = c2 * ich, ic2 = ich * ich;
+    const float rh = sqL * sqR;
+    const float unh = uh0 * n[0] + uh1 * n[1] + uh2 * n[2];
+    const float du0 = R.u0 - L.u0, du1 = R.u1 - L.u1, du2 = R.u2 - L.u2;
+    const float dun = R.un - L.un;
+    const float dp = R.p - L.p, dr = UR[0] - UL[0];
+    const float rcd = rh * ch * dun;
+    const float a1 = 0.5f * (dp - rcd) * ic2, a5 = 0.5f * (dp + rcd) * ic2, a2 = fmaf(-dp, ic2, dr);
+    float l1 = fabsf(unh - ch), l5 = fabsf(unh + ch);
+    const float l2 = fabsf(unh);
+    if (eps > 0.f) {
+        const float d = eps * ch;
+        if (l1 < d) l1 = (l1 * l1 + d * d) / (2.f * d);
+        if (l5 < d) l5 = (l5 * l5 + d * d) / (2.f * d);
+    }
+    const float w1 = l1 * a1, w2 = l2 * a2, w5 = l5 * a5;
+    const float sh0 = rh * fmaf(-dun, n[0], du0), sh1 = rh * fmaf(-dun, n[1], du1), sh2 = rh * fmaf(-dun, n[2], du2);
+    const float D0 = w1 + w2 + w5;
+    const float dw = (w5 - w1) * ch;
+    // D = |A_hat| (UR - UL): acoustic waves (u.n -+ c), entropy wave, shear
+    H[0] = fmaf(-0.5f, D0, F[0]);
+    H[1] = fmaf(-0.5f, fmaf(D0, uh0, fmaf(dw, n[0], l2 * sh0)), F[1]);
+    H[2] = fmaf(-0.5f, fmaf(D0, uh1, fmaf(dw, n[1], l2 * sh1)), F[2]);
+    H[3] = fmaf(-0.5f, fmaf(D0, uh2, fmaf(dw, n[2], l2 * sh2)), F[3]);
+    const float D4 = fmaf(w1 + w5, Hh, fmaf(dw, unh, fmaf(w2, q2, l2 * (uh0 * sh0 + uh1 * sh1 + uh2 * sh2))));
+    H[4] = fmaf(-0.5f, D4, F[4]);
+    return prim_ok(UL, L) && prim_ok(UR, R);
+}
+
+// split-f16 operand row from Nb FP32 coefficients: modes 1.. scaled by a power of two that brings
+// their largest magnitude into [8, 16); returns (mean = sqrt6 c_0, inv_beta1 / scale), the factors
+// that turn the row's MMA result (against the beta1-scaled table) into point values
 template <int P>
 __device__ __forceinline__ float2 build_row(const float* __restrict__ c, __half* A, int r, float inv_beta1) {
     using S = SPlan<P>;
@@ -271,7 +377,7 @@ __device__ __forceinline__ float2 build_row(const float* __restrict__ c, __half*
         }
         *reinterpret_cast<uint4*>(A + tc::kmajor(r, 8 * ch, K1)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    return make_float2(2.449489743f * x[0], inv_beta1 / sc);
+    return make_float2(2.449489743f * x[0], inv_beta1 * __fdividef(1.f, sc));
 }
 
 __device__ __forceinline__ void zero_row(__half* A, int r, int K1) {
@@ -307,36 +413,78 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
     if (bytes && ((uintptr_t)p & 15u) == 0) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// 4 consecutive floats (16-byte aligned when NB % 4 == 0, else element by element)
+template <bool VEC>
+__device__ __forceinline__ void load4(const float* p, float v[4]) {
+    if constexpr (VEC) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = __ldg(p + i);
+    }
+}
+
+
+// named barrier of one context (256 threads, barrier id 1 + context)
+__device__ __forceinline__ void ctx_sync(int id) { asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory"); }
+// the same barrier with an OR over the threads' predicates
+__device__ __forceinline__ bool ctx_sync_or(int id, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 256, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id)
+        : "memory");
+    return r != 0;
+}
+
+// the context's first thread polls its mbarrier; the others wait at the context barrier; false
+// (for every thread of the context) if the wait gave up
+__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t& phase, int ct, int bar_id) {
+    const bool ok = ct == 0 ? tc::mbar_wait(mbar, phase, WAIT_ITERS) : true;
+    phase ^= 1u;
+    return !ctx_sync_or(bar_id, !ok);
+}
+
 }  // namespace
 
 template <int P, int FLUX>
 __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     using S = SPlan<P>;
-    constexpr int NB = S::NB, NQ = S::NQ, NQF = S::NQF, NF = S::NF, NPT = S::NPT, NQ4 = S::NQ4;
-    constexpr int K1 = S::K1, K2 = S::K2, N1 = S::N1, NN = S::NN, N2 = S::N2, USTR = S::USTR;
+    constexpr int NB = S::NB, NQ = S::NQ, NQF = S::NQF, NQ4 = S::NQ4, NQF4 = S::NQF4, FPAD = S::FPAD;
+    constexpr int K1 = S::K1, K2 = S::K2, N1 = S::N1, NN = S::NN, N2 = S::N2, VSTR = S::VSTR, USTR = S::USTR;
+    constexpr int ELW = S::ELW;
     extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ctx = tid / CT, ct = tid - ctx * CT;   // context and thread within it
+    const int bar_id = 1 + ctx;
     const __half* sT1a = reinterpret_cast<const __half*>(smem + S::O_T1);
     const __half* sT1b = sT1a + N1 * K1;
     const __half* sT2a = reinterpret_cast<const __half*>(smem + S::O_T2);
     const __half* sT2b = sT2a + N2 * K2;
-    __half* sA1 = reinterpret_cast<__half*>(smem + S::O_AU);
-    __half* sAN = reinterpret_cast<__half*>(smem + S::O_AU + S::SZ_A1);
-    __half* sA2 = reinterpret_cast<__half*>(smem + S::O_AU);
-    float* sU = reinterpret_cast<float*>(smem + S::O_SU);
-    float* sN = reinterpret_cast<float*>(smem + S::O_SN);
-    float2* sRow = reinterpret_cast<float2*>(smem + S::O_ROW);
-    float4* sGeo = reinterpret_cast<float4*>(smem + S::O_GEO);
-    float* sFbn = reinterpret_cast<float*>(smem + S::O_FBN);
-    float* sEl = reinterpret_cast<float*>(smem + S::O_EL);
-    uint32_t* sCode = reinterpret_cast<uint32_t*>(smem + S::O_CODE);
-    uint8_t* sList = reinterpret_cast<uint8_t*>(smem + S::O_LIST);
-    int8_t* sPerm = reinterpret_cast<int8_t*>(smem + S::O_PERM);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::O_MB);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::O_MB + 8);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* cx = smem + S::O_CTX + ctx * S::CTX_BYTES;
+    __half* sA1 = reinterpret_cast<__half*>(cx + S::X_AU);
+    __half* sAN = reinterpret_cast<__half*>(cx + S::X_AU + S::SZ_A1);
+    __half* sA2 = reinterpret_cast<__half*>(cx + S::X_AU);
+    float* sU = reinterpret_cast<float*>(cx + S::X_SU);
+    float* sN = reinterpret_cast<float*>(cx + S::X_SN);
+    float2* sRow = reinterpret_cast<float2*>(cx + S::X_ROW);
+    float4* sGeo = reinterpret_cast<float4*>(cx + S::X_GEO);
+    float* sFbn = reinterpret_cast<float*>(cx + S::X_FBN);
+    float* sEl = reinterpret_cast<float*>(cx + S::X_EL);
+    int* sHdr = reinterpret_cast<int*>(cx + S::X_HDR);
+    uint32_t* sCode = reinterpret_cast<uint32_t*>(cx + S::X_CODE);
+    uint8_t* sList = reinterpret_cast<uint8_t*>(cx + S::X_LIST);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(cx + S::X_MB);
+    const int8_t* sPerm = reinterpret_cast<const int8_t*>(smem + S::O_PERM);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::O_SLOT);
     const float gamma = a.gamma;
 
-    // ---- CTA set-up: tables, zeroed operand union, permutations, barrier, tensor memory -------
+    // ---- CTA set-up: tables, zeroed context regions, permutations, barriers, tensor memory ----
     {
         const uint4* src = reinterpret_cast<const uint4*>(a.tab16);
         uint4* dst = reinterpret_cast<uint4*>(smem + S::O_T1);
@@ -344,30 +492,37 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         dst = reinterpret_cast<uint4*>(smem + S::O_T2);
         src = reinterpret_cast<const uint4*>(a.tab16 + S::G_T2);
         for (int i = tid; i < S::SZ_T2 / 16; i += MT) dst[i] = src[i];
-        uint4* z = reinterpret_cast<uint4*>(smem + S::O_AU);
-        for (int i = tid; i < S::SZ_AU / 16; i += MT) z[i] = make_uint4(0, 0, 0, 0);
-        for (int i = tid; i < 6 * NQF; i += MT) sPerm[i] = a.fperm[i];
-        if (tid == 0) tc::mbar_init(mbar);
-        if (warp == 0) tc::tmem_alloc(tslot, TMEM_COLS);
+        // every byte an MMA may read is finite
+        uint4* z = reinterpret_cast<uint4*>(smem + S::O_CTX);
+        for (int i = tid; i < 2 * S::CTX_BYTES / 16; i += MT) z[i] = make_uint4(0, 0, 0, 0);
+        int8_t* pm = reinterpret_cast<int8_t*>(smem + S::O_PERM);
+        for (int i = tid; i < 6 * NQF; i += MT) pm[i] = a.fperm[i];
     }
+    __syncthreads();
+    if (ct == 0) tc::mbar_init(mbar);
+    if (warp == 0) tc::tmem_alloc(tslot, TMEM_COLS);
     tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    const uint32_t tmem = *tslot;
+    const uint32_t tmem = *tslot + ctx * CTX_COLS;
     uint32_t phase = 0;
-    const int qq = warp & 3, part = warp >> 2;      // TMEM lane quarter, column part
-    const int lrow = qq * 32 + lane;                 // this thread's TMEM lane
+    const int wc = ct >> 5;                          // warp within the context
+    const int qq = wc & 3, part = wc >> 2;           // TMEM lane quarter (warp % 4), column part (0, 1)
+    const bool has_row = lane < 16;                  // M = 64: rows in lanes 0-15 of each quarter
+    const int lrow = 16 * qq + lane;                 // this thread's accumulator row (if has_row)
     const uint32_t lane_base = (uint32_t)(qq * 32) << 16;
 
     const int64_t ntiles = (a.ne + ET - 1) / ET;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t tstride = 2 * (int64_t)gridDim.x;
+    for (int64_t tile = 2 * (int64_t)blockIdx.x + ctx; tile < ntiles; tile += tstride) {
         const int64_t e0 = tile * ET;
         const int nel = (a.ne - e0) < (int64_t)ET ? (int)(a.ne - e0) : ET;
-        const int ncross = __ldg(a.tcnt + 2 * tile), nwork = __ldg(a.tcnt + 2 * tile + 1);
-        // ---- L2 prefetch of this CTA's next tile (contiguous blocks) -------------------------------
-        if (tid == 0) {
-            const int64_t nt = tile + gridDim.x;
+        const int32_t* hdr = a.thdr + tile * THDR;
+        const int ncross = __ldg(hdr), nwork = __ldg(hdr + 1), nblk = __ldg(hdr + 2);
+        // ---- L2 prefetch of this context's next tile (contiguous blocks) ---------------------------
+        if (ct == 0) {
+            const int64_t nt = tile + tstride;
             if (nt < ntiles) {
                 const int64_t n0 = nt * ET;
                 const int nn = (a.ne - n0) < (int64_t)ET ? (int)(a.ne - n0) : ET;
@@ -381,202 +536,208 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                     }
                 }
                 prefetch_l2(a.jinv + n0 * 9, (uint32_t)(nn * 36));
+                prefetch_l2(a.xnbr + nt * SLOTS, SLOTS * 4);
+                prefetch_l2(a.slot + nt * SLOTS, SLOTS * 4);
             }
         }
-        // ---- build: operand rows, per-face and per-element quantities, tile metadata --------------
-        if (tid < 128) {
-            const int r = tid;
+        // ---- build: operand rows, per-element quantities, tile metadata ---------------------------
+        if (ct < 64) {
+            const int r = ct;
             if (r < 5 * nel) {
                 const int e = r / 5, v = r - 5 * e;
                 sRow[r] = build_row<P>(a.U_hi + ((e0 + e) * 5 + v) * NB, sA1, r, a.inv_beta1);
             } else {
                 zero_row(sA1, r, K1);
             }
-            if (tid < SLOTS) {
-                // face geometry and the element's mean-state normal flux, scaled for operand A2
-                const int s = tid, e = s >> 2, f = s & 3;
-                if (e < nel) {
-                    float I[9], ub[5];
-                    const float* Ig = a.jinv + (e0 + e) * 9;
+        } else if (ct < 64 + ET) {
+            // per element: J^-1, its flux-scaled copy, the mean state's flux and scaled
+            // contravariant flux, the scale and the epilogue factor
+            const int e = ct - 64;
+            if (e < nel) {
+                float I[9], ub[5];
+                const float* Ig = a.jinv + (e0 + e) * 9;
 #pragma unroll
-                    for (int t = 0; t < 9; ++t) I[t] = __ldg(Ig + t);
+                for (int t = 0; t < 9; ++t) I[t] = __ldg(Ig + t);
 #pragma unroll
-                    for (int v = 0; v < 5; ++v) ub[v] = 2.449489743f * __ldg(a.U_hi + ((e0 + e) * 5 + v) * NB);
-                    const float ts = elem_flux_scale(ub, I, gamma);
-                    float g0, g1, g2;
-                    grad_lambda(I, f, g0, g1, g2);
-                    const float sf = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
-                    const float ninv = -1.f / sf;
-                    const float n0 = g0 * ninv, n1 = g1 * ninv, n2 = g2 * ninv;
-                    float F[3][5];
-                    euler_fluxes(ub, gamma, F);
-                    const float sc = -sf * ts;
-                    sGeo[s] = make_float4(n0, n1, n2, sc);
+                for (int v = 0; v < 5; ++v) ub[v] = 2.449489743f * __ldg(a.U_hi + ((e0 + e) * 5 + v) * NB);
+                const float ts = elem_flux_scale(ub, I, gamma);
+                float* el = sEl + e * ELW;
 #pragma unroll
-                    for (int v = 0; v < 5; ++v) sFbn[s * 5 + v] = sc * (F[0][v] * n0 + F[1][v] * n1 + F[2][v] * n2);
+                for (int t = 0; t < 9; ++t) {
+                    el[t] = I[t];
+                    el[9 + t] = ts * I[t];
                 }
-            } else if (tid < SLOTS + ET) {
-                // scaled J^-1 and the scaled contravariant flux of the mean state (volume term)
-                const int e = tid - SLOTS;
-                if (e < nel) {
-                    float I[9], ub[5];
-                    const float* Ig = a.jinv + (e0 + e) * 9;
+                float G[3][5], F[3][5];
+                contravariant(ub, el + 9, gamma, G);
+                euler_fluxes(ub, gamma, F);
 #pragma unroll
-                    for (int t = 0; t < 9; ++t) I[t] = __ldg(Ig + t);
+                for (int k = 0; k < 3; ++k)
 #pragma unroll
-                    for (int v = 0; v < 5; ++v) ub[v] = 2.449489743f * __ldg(a.U_hi + ((e0 + e) * 5 + v) * NB);
-                    const float ts = elem_flux_scale(ub, I, gamma);
-                    float* el = sEl + e * 28;
-#pragma unroll
-                    for (int t = 0; t < 9; ++t) el[t] = ts * I[t];
-                    float G[3][5];
-                    contravariant(ub, el, gamma, G);
-#pragma unroll
-                    for (int k = 0; k < 3; ++k)
-#pragma unroll
-                        for (int v = 0; v < 5; ++v) el[9 + 5 * k + v] = G[k][v];
-                    el[24] = a.inv_beta2 / ts;
-                }
+                    for (int v = 0; v < 5; ++v) {
+                        el[18 + 5 * k + v] = G[k][v];
+                        el[33 + 5 * k + v] = F[k][v];
+                    }
+                el[48] = ts;
+                el[49] = a.inv_beta2 * __fdividef(1.f, ts);
             }
-        } else {
-            const int t2 = tid - 128;
+        } else if (ct >= 80 && ct < 80 + SLOTS) {
+            const int t2 = ct - 80;
             const uint8_t* tl = a.tlist + tile * (2 * SLOTS);
-            if (t2 < SLOTS) {
-                sCode[t2] = __ldg(a.slot + tile * SLOTS + t2);
-                sList[t2] = __ldg(tl + t2);
-                sList[SLOTS + t2] = __ldg(tl + SLOTS + t2);
-            }
-            // neighbour operand rows of the faces to other tiles: row (c, v) of block c / PB
-            for (int rr = t2; rr < 5 * ncross; rr += MT - 128) {
+            sCode[t2] = __ldg(a.slot + tile * SLOTS + t2);
+            sList[t2] = __ldg(tl + t2);
+            sList[SLOTS + t2] = __ldg(tl + SLOTS + t2);
+            if (t2 < THDR) sHdr[t2] = __ldg(hdr + t2);
+        } else if (ct >= 128) {
+            // neighbour operand rows of the faces to other tiles, grouped in blocks of one
+            // neighbour face: row R_b + 5 i + v for the i-th pair of block b
+            for (int rr = ct - 128; rr < 5 * ncross; rr += CT - 128) {
                 const int c = rr / 5, v = rr - 5 * c;
-                const int s = __ldg(tl + c);
-                const int e = s >> 2, f = s & 3;
-                const int64_t n = __ldg(a.nbr + (e0 + e) * 4 + f);
-                const int b = c / PB, lr = rr - 5 * PB * b;
-                sRow[128 + 128 * b + lr] = build_row<P>(a.U_hi + (n * 5 + v) * NB, sAN + b * 128 * K1, lr, a.inv_beta1);
+                const int64_t n = __ldg(a.xnbr + tile * SLOTS + c);
+                int row = 0;
+                for (int b = 0; b < nblk; ++b) {
+                    const int d = __ldg(hdr + 3 + b);
+                    const int cs = (d >> 17) & 127, np = (d >> 12) & 31;
+                    if (c >= cs && c < cs + np) row = ((d >> 2) & 1023) + 5 * (c - cs) + v;
+                }
+                sRow[64 + row] = build_row<P>(a.U_hi + (n * 5 + v) * NB, sAN, row, a.inv_beta1);
             }
         }
         tc::fence_async_smem();
         tc::fence_before();
-        __syncthreads();
+        ctx_sync(bar_id);
         tc::fence_after();
-        const int nblk = (ncross + PB - 1) / PB;
         // ---- MMA 1: own values at all points, neighbours' traces ----------------------------------
         // D = A x [phi_hi, phi_hi] + A x [phi_lo, 0] = (x_hi + x_lo) phi_hi + x_hi phi_lo
-        if (tid == 0) {
-            const uint32_t id1 = tc::idesc_f16(128, N1), idn = tc::idesc_f16(128, NN);
+        if (ct == 0) {
+            const uint32_t id1 = tc::idesc_f16(64, N1), idn = tc::idesc_f16(64, NN);
 #pragma unroll
             for (int h = 0; h < 2; ++h)
 #pragma unroll
                 for (int ks = 0; ks < K1 / 16; ++ks)
                     tc::mma(tmem + S::C_D1, tc::kdesc(sA1, ks, K1), tc::kdesc(h ? sT1b : sT1a, ks, K1), id1,
                             (h | ks) != 0);
-            for (int b = 0; b < nblk; ++b)
+            for (int b = 0; b < nblk; ++b) {
+                const int d = sHdr[3 + b];
+                const __half* Ab = sAN + tc::kmajor((d >> 2) & 1023, 0, K1);   // first row: a multiple of 8
+                const int toff = tc::kmajor(FPAD * (d & 3), 0, K1);            // face slice of table 1
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
 #pragma unroll
                     for (int ks = 0; ks < K1 / 16; ++ks)
-                        tc::mma(tmem + S::C_DN + b * NN, tc::kdesc(sAN + b * 128 * K1, ks, K1),
-                                tc::kdesc(h ? sT1b : sT1a, ks, K1), idn, (h | ks) != 0);
+                        tc::mma(tmem + S::C_DN + b * NN, tc::kdesc(Ab, ks, K1), tc::kdesc((h ? sT1b : sT1a) + toff, ks, K1),
+                                idn, (h | ks) != 0);
+            }
             tc::commit(mbar);
         }
-        if (!tc_wait(mbar, phase)) {
-            if (tid == 0) atomicOr(a.status, 2u);
+        // per face while the tensor cores work: outward normal, |grad lambda_f| times the element's
+        // flux scale, and the mean state's scaled normal flux
+        if (ct < SLOTS) {
+            const int s = ct, e = s >> 2, f = s & 3;
+            if (e < nel) {
+                const float* el = sEl + e * ELW;
+                float g0, g1, g2;
+                grad_lambda(el, f, g0, g1, g2);
+                const float isf = rsqrtf(g0 * g0 + g1 * g1 + g2 * g2);
+                const float n0 = -g0 * isf, n1 = -g1 * isf, n2 = -g2 * isf;
+                const float sc = -el[48] * __fdividef(1.f, isf);
+                sGeo[s] = make_float4(n0, n1, n2, sc);
+                const float* F = el + 33;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) sFbn[s * 5 + v] = sc * (F[v] * n0 + F[5 + v] * n1 + F[10 + v] * n2);
+            }
+        }
+        if (!tc_wait(mbar, phase, ct, bar_id)) {
+            if (ct == 0) atomicOr(a.status, 2u);
             break;
         }
         tc::fence_after();
-        // ---- stage TMEM -> shared memory: point states (mean + deviation / scale) ----------------
+        // ---- stage TMEM -> shared memory: point states (mean + deviation x factor) ----------------
         {
-            const bool own_ok = lrow < 5 * nel;
+            const bool own_ok = has_row && lrow < 5 * nel;
             const int e = lrow / 5, v = lrow - 5 * (lrow / 5);
-            const float2 mr = sRow[lrow];
-            float* dst = sU + e * USTR + v;
-            for (int ch = part; ch * 8 < NPT; ch += 4) {
+            const float2 mr = own_ok ? sRow[lrow] : make_float2(0.f, 0.f);
+            float* dst = sU + e * USTR + v * VSTR;
+            for (int ch = part; ch * 8 < S::NPT; ch += 2) {
                 float val[8];
                 tc::ld8(tmem + lane_base + S::C_D1 + 8 * ch, val);
                 if (own_ok) {
 #pragma unroll
-                    for (int t = 0; t < 8; ++t)
-                        if (8 * ch + t < NPT) dst[(8 * ch + t) * 5] = fmaf(val[t], mr.y, mr.x);
+                    for (int t = 0; t < 8; ++t) val[t] = fmaf(val[t], mr.y, mr.x);
+                    *reinterpret_cast<float4*>(dst + 8 * ch) = make_float4(val[0], val[1], val[2], val[3]);
+                    *reinterpret_cast<float4*>(dst + 8 * ch + 4) = make_float4(val[4], val[5], val[6], val[7]);
                 }
             }
-            const int b = part;
-            if (b < nblk) {
-                const int c = b * PB + lrow / 5;
-                const bool ok = lrow < 5 * PB && c < ncross;
-                int fn = 0;
-                float2 nr = make_float2(0.f, 0.f);
-                if (ok) {
-                    fn = (sCode[sList[c]] >> 19) & 3;
-                    nr = sRow[128 + 128 * b + lrow];
-                }
-                float* nd = sN + (c * NQF - fn * NQF) * 5 + v;
+            for (int b = part; b < nblk; b += 2) {
+                const int d = sHdr[3 + b];
+                const int R0 = (d >> 2) & 1023, npair = (d >> 12) & 31, cs = (d >> 17) & 127;
+                float val[16];
+                tc::ld16(tmem + lane_base + S::C_DN + b * NN, val);
+                if (has_row && lrow < 5 * npair) {
+                    const float2 nr = sRow[64 + R0 + lrow];
+                    float* nd = sN + ((cs + lrow / 5) * 5 + v) * NQF4;
 #pragma unroll
-                for (int ch = 0; ch < NN / 16; ++ch) {
-                    float val[16];
-                    tc::ld16(tmem + lane_base + S::C_DN + b * NN + 16 * ch, val);
-#pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        const int n = 16 * ch + t;
-                        if (ok && n < NF && n / NQF == fn) nd[n * 5] = fmaf(val[t], nr.y, nr.x);
-                    }
+                    for (int t = 0; t < NQF4; t += 4)
+                        *reinterpret_cast<float4*>(nd + t) =
+                            make_float4(fmaf(val[t], nr.y, nr.x), fmaf(val[t + 1], nr.y, nr.x),
+                                        fmaf(val[t + 2], nr.y, nr.x), fmaf(val[t + 3], nr.y, nr.x));
                 }
             }
         }
         tc::fence_before();
-        __syncthreads();
+        ctx_sync(bar_id);
         // ---- fluxes -> operand A2 (row (e, v); K: volume (k, q), then face (f, q)) ---------------
         {
-            constexpr int NV = NQ4 * ET;   // volume items, a multiple of 32
+            // volume items: lanes = 8 elements x 4 consecutive points (conflict-free 32-bit
+            // operand stores), two element groups (the second half full)
+            constexpr int NV = NQ4 * 16;
             const int nitems = NV + nwork * NQF;
-            for (int i = tid; i < nitems; i += MT) {
+            for (int i = ct; i < nitems; i += CT) {
                 if (i < NV) {
-                    // lanes: 8 elements x 4 consecutive points (conflict-free 32-bit operand stores)
                     const int wi = i >> 5, ln = i & 31;
-                    const int g = wi / (ET / 8), eb = wi - g * (ET / 8);
+                    const int g = wi >> 1, eb = wi & 1;
                     const int e = eb * 8 + (ln >> 2), q = g * 4 + (ln & 3);
                     if (e >= nel || q >= NQ) continue;
-                    const float* u = sU + e * USTR + (NF + q) * 5;
-                    const float U[5] = {u[0], u[1], u[2], u[3], u[4]};
-                    if (!phys_ok(U, gamma)) atomicOr(a.status, 1u);
-                    const float* el = sEl + e * 28;
+                    const float* u = sU + e * USTR + 4 * FPAD + q;
+                    const float U[5] = {u[0], u[VSTR], u[2 * VSTR], u[3 * VSTR], u[4 * VSTR]};
+                    if (!phys_ok(U)) atomicOr(a.status, 1u);
+                    const float* el = sEl + e * ELW;
                     float G[3][5];
-                    contravariant(U, el, gamma, G);
+                    contravariant(U, el + 9, gamma, G);
 #pragma unroll
                     for (int k = 0; k < 3; ++k)
 #pragma unroll
                         for (int v = 0; v < 5; ++v)
-                            *opword(sA2, e * 5 + v, k * NQ + q, K2) = split_pair(G[k][v] - el[9 + 5 * k + v]);
+                            *opword(sA2, e * 5 + v, k * NQ + q, K2) = split_pair(G[k][v] - el[18 + 5 * k + v]);
                 } else {
                     const int j = i - NV;
                     const int w = j / NQF, q = j - w * NQF;
                     const int s = sList[SLOTS + w];
                     const uint32_t code = sCode[s];
                     const int kind = code & 3, e = s >> 2, f = s & 3;
-                    const float* um = sU + e * USTR + (f * NQF + q) * 5;
-                    const float Um[5] = {um[0], um[1], um[2], um[3], um[4]};
+                    const float* um = sU + e * USTR + FPAD * f + q;
+                    const float Um[5] = {um[0], um[VSTR], um[2 * VSTR], um[3 * VSTR], um[4 * VSTR]};
                     const float4 geo = sGeo[s];
                     const float nv[3] = {geo.x, geo.y, geo.z};
                     const int pq = sPerm[((code >> 9) & 7) * NQF + q];
                     const int sp = (code >> 2) & 127;
                     float Up[5];
                     if (kind == SK_OWN) {
-                        const float* up = sU + (sp >> 2) * USTR + ((sp & 3) * NQF + pq) * 5;
+                        const float* up = sU + (sp >> 2) * USTR + FPAD * (sp & 3) + pq;
 #pragma unroll
-                        for (int v = 0; v < 5; ++v) Up[v] = up[v];
+                        for (int v = 0; v < 5; ++v) Up[v] = up[v * VSTR];
                     } else if (kind == SK_CROSS) {
-                        const float* up = sN + (((code >> 12) & 127) * NQF + pq) * 5;
+                        const float* up = sN + ((code >> 12) & 127) * 5 * NQF4 + pq;
 #pragma unroll
-                        for (int v = 0; v < 5; ++v) Up[v] = up[v];
+                        for (int v = 0; v < 5; ++v) Up[v] = up[v * NQF4];
                     } else if (((code >> 21) & 3) == DG_BC_WALL) {
                         wall_ghost(Um, nv, Up);
                     } else {
                         farfield_ghost(Um, nv, a.finf, gamma, Up);
                     }
-                    if (!phys_ok(Um, gamma) || !phys_ok(Up, gamma)) atomicOr(a.status, 1u);
                     float H[5];
-                    if (FLUX == DG_ROE) roe_flux(Um, Up, nv, gamma, a.roe_eps, H);
-                    else rusanov_flux(Um, Up, nv, gamma, H);
+                    const bool ok = FLUX == DG_ROE ? roe_f32(Um, Up, nv, gamma, a.roe_eps, H)
+                                                   : rusanov_f32(Um, Up, nv, gamma, H);
+                    if (!ok) atomicOr(a.status, 1u);
                     const float* fb = sFbn + s * 5;
 #pragma unroll
                     for (int v = 0; v < 5; ++v)
@@ -594,11 +755,11 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         }
         tc::fence_async_smem();
         tc::fence_before();
-        __syncthreads();
+        ctx_sync(bar_id);
         tc::fence_after();
         // ---- MMA 2: projection onto the weighted basis gradients + face lift ----------------------
-        if (tid == 0) {
-            const uint32_t id2 = tc::idesc_f16(128, N2);
+        if (ct == 0) {
+            const uint32_t id2 = tc::idesc_f16(64, N2);
             constexpr int KS = K2 / 16, KH = KS / 2;
 #pragma unroll 1
             for (int ks = 0; ks < KS; ++ks) {
@@ -612,51 +773,64 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         }
         // epilogue operands in flight while the tensor cores work: 4-mode chunks of this thread's row
         constexpr int NCH = S::NCH;
-        const bool row_ok = lrow < 5 * nel;
+        constexpr bool VEC = NB % 4 == 0;
+        const bool row_ok = has_row && lrow < 5 * nel;
         const int ee = lrow / 5, vv = lrow - 5 * (lrow / 5);
         const int64_t gbase = (e0 + ee) * 5 * NB + vv * NB;
-        float uh[2][4], ul[2][4], u0h[2][4], u0l[2][4];
-        int nchunk = 0, chs[2] = {part, part + 4};
+        // chunks part, part + 2, part + 4 of this thread's row
+        const int nchunk = part < NCH ? (NCH - part + 1) / 2 : 0;
+        float uh[3][4], ul[3][4], u0h[3][4], u0l[3][4];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            if (chs[k] < NCH) nchunk = k + 1;
-        }
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) uh[k][t] = ul[k][t] = u0h[k][t] = u0l[k][t] = 0.f;
         if (row_ok && a.mode != 0) {
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < 3; ++k) {
                 if (k >= nchunk) break;
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int jj = 4 * chs[k] + t;
-                    const bool in = jj < NB;
-                    uh[k][t] = in ? __ldg(a.U_hi + gbase + jj) : 0.f;
-                    ul[k][t] = in ? __ldg(a.U_lo + gbase + jj) : 0.f;
-                    u0h[k][t] = (in && a.a != 0.f) ? __ldg(a.U0_hi + gbase + jj) : 0.f;
-                    u0l[k][t] = (in && a.a != 0.f) ? __ldg(a.U0_lo + gbase + jj) : 0.f;
+                const int ch = part + 2 * k;
+                const int64_t o = gbase + 4 * ch;
+                if (VEC || 4 * ch + 4 <= NB) {
+                    load4<VEC>(a.U_hi + o, uh[k]);
+                    load4<VEC>(a.U_lo + o, ul[k]);
+                    if (a.a != 0.f) {
+                        load4<VEC>(a.U0_hi + o, u0h[k]);
+                        load4<VEC>(a.U0_lo + o, u0l[k]);
+                    }
+                } else {
+                    for (int t = 0; 4 * ch + t < NB; ++t) {
+                        uh[k][t] = __ldg(a.U_hi + o + t);
+                        ul[k][t] = __ldg(a.U_lo + o + t);
+                        if (a.a != 0.f) {
+                            u0h[k][t] = __ldg(a.U0_hi + o + t);
+                            u0l[k][t] = __ldg(a.U0_lo + o + t);
+                        }
+                    }
                 }
             }
         }
-        if (!tc_wait(mbar, phase)) {
-            if (tid == 0) atomicOr(a.status, 2u);
+        if (!tc_wait(mbar, phase, ct, bar_id)) {
+            if (ct == 0) atomicOr(a.status, 2u);
             break;
         }
         tc::fence_after();
         // ---- epilogue: residual, or the RK stage in float-float -----------------------------------
         {
-            const float inv = row_ok ? sEl[ee * 28 + 24] : 0.f;
+            const float inv = row_ok ? sEl[ee * ELW + 49] : 0.f;
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < 3; ++k) {
                 if (k >= nchunk) break;
+                const int ch = part + 2 * k;
                 float d0[4], d1[4];
-                ld4x2(tmem + lane_base + S::C_D2 + 4 * chs[k], tmem + lane_base + S::C_D2 + N2 + 4 * chs[k], d0, d1);
+                ld4x2(tmem + lane_base + S::C_D2 + 4 * ch, tmem + lane_base + S::C_D2 + N2 + 4 * ch, d0, d1);
                 if (!row_ok) continue;
+                float oh[4], ol[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const int jj = 4 * chs[k] + t;
-                    if (jj >= NB) continue;
                     const float R = (d0[t] + d1[t]) * inv;
                     if (a.mode == 0) {
-                        a.out_hi[gbase + jj] = R;
+                        oh[t] = R;
+                        ol[t] = 0.f;
                     } else {
                         // out = U + a (U0 - U) + b dt R: increment in FP32, float-float sum with U
                         const float dlt = fmaf(a.a, (u0h[k][t] - uh[k][t]) + (u0l[k][t] - ul[k][t]), a.bdt * R);
@@ -664,21 +838,32 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                         const float bb = sm - uh[k][t];
                         float err = (uh[k][t] - (sm - bb)) + (dlt - bb);
                         err += ul[k][t];
-                        const float hh = sm + err;
-                        a.out_hi[gbase + jj] = hh;
-                        a.out_lo[gbase + jj] = err - (hh - sm);
+                        oh[t] = sm + err;
+                        ol[t] = err - (oh[t] - sm);
+                    }
+                }
+                const int64_t o = gbase + 4 * ch;
+                if (VEC) {
+                    *reinterpret_cast<float4*>(a.out_hi + o) = make_float4(oh[0], oh[1], oh[2], oh[3]);
+                    if (a.mode != 0) *reinterpret_cast<float4*>(a.out_lo + o) = make_float4(ol[0], ol[1], ol[2], ol[3]);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        if (4 * ch + t >= NB) break;
+                        a.out_hi[o + t] = oh[t];
+                        if (a.mode != 0) a.out_lo[o + t] = ol[t];
                     }
                 }
             }
         }
         tc::fence_before();
-        __syncthreads();
+        ctx_sync(bar_id);
         tc::fence_after();
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
+    if (warp == 0) tc::tmem_dealloc(*tslot, TMEM_COLS);
 }
 
 namespace {
@@ -694,7 +879,7 @@ cudaError_t slaunch(const StageArgs& sa, cudaStream_t s, int nsm) {
         init = true;
     }
     const int64_t ntiles = (sa.ne + ET - 1) / ET;
-    k<<<(int)std::min<int64_t>(ntiles, (int64_t)nsm), MT, S::BYTES, s>>>(sa);
+    k<<<(int)std::min<int64_t>((ntiles + 1) / 2, (int64_t)nsm), MT, S::BYTES, s>>>(sa);
     return cudaGetLastError();
 }
 
@@ -711,8 +896,9 @@ int mixed_tab_halves(int p) {
 // f16 operand images of the basis tables in the canonical K-major layout, for
 // operands that hold interleaved (hi, lo) pairs at positions (2k, 2k+1):
 //   T1a / T1b [N1 points][K1]: (beta1 phi_hi, beta1 phi_hi) at mode j for point n
-//       (face points f*Nqf+q first, then volume points); T1b: (beta1 phi_lo, 0);
-//       mode 0 is zero (the operands carry modes 1.. only)
+//       (face f point q at row FPAD f + q, so that each face's rows start on an 8-row core
+//       matrix boundary; then the volume points); T1b: (beta1 phi_lo, 0); mode 0 is zero
+//       (the operands carry modes 1.. only)
 //   T2a / T2b [N2 modes][K2]: logical k = (kk, q) -> beta2 w_q d_kk phi_j (q < Nq),
 //       then (f, q) -> beta2 wf_q phi_j on face f; (hi, hi) in T2a and (lo, 0) in T2b
 template <int P>
@@ -720,12 +906,14 @@ static void build_mixed_tables_t(const RefData& ref, std::vector<uint16_t>& out,
     using S = SPlan<P>;
     const TabLayout L(P);
     const double* t = ref.tab.data();
+    // own-point row n: face f point q at n = FPAD f + q (rows FPAD f + Nqf .. FPAD f + FPAD - 1
+    // zero), volume point q at n = 4 FPAD + q
     auto phi_pt = [&](int n, int j) -> double {
-        if (n < S::NF) {
-            const int f = n / S::NQF, q = n % S::NQF;
-            return t[L.phif + (f * S::NB + j) * S::NQF + q];
+        if (n < 4 * S::FPAD) {
+            const int f = n / S::FPAD, q = n % S::FPAD;
+            return q < S::NQF ? t[L.phif + (f * S::NB + j) * S::NQF + q] : 0.0;
         }
-        return t[L.phiq + j * S::NQ + (n - S::NF)];
+        return t[L.phiq + j * S::NQ + (n - 4 * S::FPAD)];
     };
     auto t2 = [&](int j, int kk) -> double {
         if (kk < 3 * S::NQ) {
@@ -774,16 +962,19 @@ void build_mixed_tables(int p, const RefData& ref, std::vector<uint16_t>& out, f
 }
 
 // Tile metadata of the fused kernel (host, once per mesh): for every tile of ET consecutive
-// internal elements, the slot codes, the list of faces to other tiles (cross list, in cross
-// index order) and the list of faces whose flux the tile evaluates (work list), and both counts.
+// internal elements, the slot codes, the list of faces to other tiles (ordered by the neighbour's
+// local face; cross index = position in this list), the list of faces whose flux the tile
+// evaluates (work list), and the tile header (counts and neighbour operand blocks).
 void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vector<uint8_t>& lists,
-                       std::vector<int32_t>& cnt) {
+                       std::vector<int32_t>& hdr, std::vector<int32_t>& xnbr) {
     const int64_t ne = h.ne, ntiles = (ne + ET - 1) / ET;
     slot.assign((size_t)ntiles * SLOTS, (uint32_t)SK_SKIP);
     lists.assign((size_t)ntiles * 2 * SLOTS, 0);
-    cnt.assign((size_t)ntiles * 2, 0);
+    hdr.assign((size_t)ntiles * THDR, 0);
+    xnbr.assign((size_t)ntiles * SLOTS, 0);
     for (int64_t t = 0; t < ntiles; ++t) {
-        int nc = 0, nw = 0;
+        std::vector<int> cross[4];
+        int nw = 0;
         for (int s = 0; s < SLOTS; ++s) {
             const int64_t e = t * ET + (s >> 2);
             if (e >= ne) break;
@@ -797,14 +988,29 @@ void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vect
                 const int sp = (int)(n - t * ET) * 4 + (int)(fc & 3);
                 code = (sp > s ? SK_OWN : SK_SKIP) | ((uint32_t)sp << 2) | ((fc >> 2) << 9);
             } else {
-                code = SK_CROSS | ((fc >> 2) << 9) | ((uint32_t)nc << 12) | ((fc & 3) << 19);
-                lists[(size_t)t * 2 * SLOTS + nc++] = (uint8_t)s;
+                code = SK_CROSS | ((fc >> 2) << 9);
+                cross[fc & 3].push_back(s);
             }
             slot[(size_t)t * SLOTS + s] = code;
             if ((code & 3) != SK_SKIP) lists[(size_t)t * 2 * SLOTS + SLOTS + nw++] = (uint8_t)s;
         }
-        cnt[2 * t] = nc;
-        cnt[2 * t + 1] = nw;
+        int nc = 0, nb = 0, row = 0;
+        int32_t* H = hdr.data() + (size_t)t * THDR;
+        for (int fn = 0; fn < 4; ++fn)
+            for (size_t k0 = 0; k0 < cross[fn].size(); k0 += PB) {
+                const int np = (int)std::min<size_t>(PB, cross[fn].size() - k0);
+                H[3 + nb++] = fn | (row << 2) | (np << 12) | (nc << 17);
+                for (int k = 0; k < np; ++k) {
+                    const int s = cross[fn][k0 + k];
+                    slot[(size_t)t * SLOTS + s] |= (uint32_t)nc << 12;
+                    xnbr[(size_t)t * SLOTS + nc] = h.nbr[(t * ET + (s >> 2)) * 4 + (s & 3)];
+                    lists[(size_t)t * 2 * SLOTS + nc++] = (uint8_t)s;
+                }
+                row = (row + 5 * np + 7) / 8 * 8;
+            }
+        H[0] = nc;
+        H[1] = nw;
+        H[2] = nb;
     }
 }
 
@@ -819,10 +1025,10 @@ cudaError_t launch_residual_mixed(dg_mesh* m, const float* U_hi, const float* U_
     r.out_hi = out_hi;
     r.out_lo = out_lo;
     r.jinv = static_cast<const float*>(m->d_jinv);
-    r.nbr = m->d_nbr;
     r.slot = m->d_mslot;
     r.tlist = m->d_mlist;
-    r.tcnt = m->d_mcnt;
+    r.thdr = m->d_mhdr;
+    r.xnbr = m->d_mxnbr;
     r.fperm = m->d_fperm;
     r.tab16 = m->d_tab16;
     r.ne = m->host.ne;
