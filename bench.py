@@ -113,13 +113,14 @@ def algorithmic_model(p, ne, flux, s_state, stage):
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the fused stage kernel from one
 # ncu capture of the 32^3 x 6 P3 Roe vortex case (three consecutive stage launches, mean bytes
-# per element per launch), with the hash of the sources the kernel was built from.  Traffic
+# per element per launch; Morton order for the mixed kernel, RCM for FP64), with the hash of the
+# sources the kernel was built from.  Traffic
 # grows in proportion to the element count (one pass over the element-ordered state), so the
 # bench scales it to the workload's tets; it reports null when the sources changed since.
 MEASURED_TRAFFIC = {
     # (precision, p, flux): (bytes per element per launch, source files, sha256[:16] of them)
-    ("mixed", 3, "roe"): (1988.90, ("kernels_mixed.cu", "tc_ops.cuh", "euler_device.cuh", "dg_internal.h"),
-                          "0173ab84e41f9364"),
+    ("mixed", 3, "roe"): (2056.0, ("kernels_mixed.cu", "tc_ops.cuh", "euler_device.cuh", "dg_internal.h"),
+                          "4244c867bd3834d3"),
     ("f64", 3, "roe"): (2072.10, ("kernels_simt.cu", "euler_device.cuh", "dg_internal.h"), "7298101050ccbf46"),
 }
 
@@ -383,7 +384,7 @@ def cpu_baseline_subprocess(workload, nsample, reps=1):
                       f"states), {reps} evaluation(s), {sec:.1f}s each, 1 thread"}
 
 
-SAMPLE = {"c1": 1296, "c2": 60000, "c3": 30000, "c4": 60000, "c5": 30000, "c3s": 30000}
+SAMPLE = {"c1": 1296, "c2": 120000, "c3": 60000, "c4": 120000, "c5": 60000, "c3s": 60000}
 
 
 def run_reference(args):
@@ -549,7 +550,7 @@ def run_study(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64", "fp32"])

@@ -549,37 +549,6 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
             } else {
                 zero_row(sA1, r, K1);
             }
-        } else if (ct < 64 + ET) {
-            // per element: J^-1, its flux-scaled copy, the mean state's flux and scaled
-            // contravariant flux, the scale and the epilogue factor
-            const int e = ct - 64;
-            if (e < nel) {
-                float I[9], ub[5];
-                const float* Ig = a.jinv + (e0 + e) * 9;
-#pragma unroll
-                for (int t = 0; t < 9; ++t) I[t] = __ldg(Ig + t);
-#pragma unroll
-                for (int v = 0; v < 5; ++v) ub[v] = 2.449489743f * __ldg(a.U_hi + ((e0 + e) * 5 + v) * NB);
-                const float ts = elem_flux_scale(ub, I, gamma);
-                float* el = sEl + e * ELW;
-#pragma unroll
-                for (int t = 0; t < 9; ++t) {
-                    el[t] = I[t];
-                    el[9 + t] = ts * I[t];
-                }
-                float G[3][5], F[3][5];
-                contravariant(ub, el + 9, gamma, G);
-                euler_fluxes(ub, gamma, F);
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-#pragma unroll
-                    for (int v = 0; v < 5; ++v) {
-                        el[18 + 5 * k + v] = G[k][v];
-                        el[33 + 5 * k + v] = F[k][v];
-                    }
-                el[48] = ts;
-                el[49] = a.inv_beta2 * __fdividef(1.f, ts);
-            }
         } else if (ct >= 80 && ct < 80 + SLOTS) {
             const int t2 = ct - 80;
             const uint8_t* tl = a.tlist + tile * (2 * SLOTS);
@@ -629,7 +598,45 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
             }
             tc::commit(mbar);
         }
-        // per face while the tensor cores work: outward normal, |grad lambda_f| times the element's
+        // per element while the tensor cores work (used by the faces below and the flux phase)
+        if (ct >= 64 && ct < 64 + ET) {
+            // per element: J^-1, its flux-scaled copy, the mean state's flux and scaled
+            // contravariant flux, the scale and the epilogue factor
+            const int e = ct - 64;
+            if (e < nel) {
+                float I[9], ub[5];
+                const float* Ig = a.jinv + (e0 + e) * 9;
+#pragma unroll
+                for (int t = 0; t < 9; ++t) I[t] = __ldg(Ig + t);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) ub[v] = 2.449489743f * __ldg(a.U_hi + ((e0 + e) * 5 + v) * NB);
+                const float ts = elem_flux_scale(ub, I, gamma);
+                float* el = sEl + e * ELW;
+#pragma unroll
+                for (int t = 0; t < 9; ++t) {
+                    el[t] = I[t];
+                    el[9 + t] = ts * I[t];
+                }
+                float G[3][5], F[3][5];
+                contravariant(ub, el + 9, gamma, G);
+                euler_fluxes(ub, gamma, F);
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) {
+                        el[18 + 5 * k + v] = G[k][v];
+                        el[33 + 5 * k + v] = F[k][v];
+                    }
+                el[48] = ts;
+                el[49] = a.inv_beta2 * __fdividef(1.f, ts);
+            }
+        }
+        if (!tc_wait(mbar, phase, ct, bar_id)) {
+            if (ct == 0) atomicOr(a.status, 2u);
+            break;
+        }
+        tc::fence_after();
+        // per face (before the staging): outward normal, |grad lambda_f| times the element's
         // flux scale, and the mean state's scaled normal flux
         if (ct < SLOTS) {
             const int s = ct, e = s >> 2, f = s & 3;
@@ -646,11 +653,6 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 for (int v = 0; v < 5; ++v) sFbn[s * 5 + v] = sc * (F[v] * n0 + F[5 + v] * n1 + F[10 + v] * n2);
             }
         }
-        if (!tc_wait(mbar, phase, ct, bar_id)) {
-            if (ct == 0) atomicOr(a.status, 2u);
-            break;
-        }
-        tc::fence_after();
         // ---- stage TMEM -> shared memory: point states (mean + deviation x factor) ----------------
         {
             const bool own_ok = has_row && lrow < 5 * nel;
