@@ -388,6 +388,10 @@ __device__ __forceinline__ void zero_row(__half* A, int r, int K1) {
 __device__ __forceinline__ uint32_t* opword(__half* A, int r, int kw, int K) {
     return reinterpret_cast<uint32_t*>(A + tc::kmajor(r, 2 * kw, K));
 }
+// the same word split into a row part and a K part of the half index: kmajor(r, 2 kw, K) =
+// rowpart(r, K) + kpart(kw)
+__host__ __device__ constexpr int rowpart(int r, int K) { return (r >> 3) * (K >> 3) * 64 + (r & 7) * 8; }
+__device__ __forceinline__ int kpart(int kw) { return (kw >> 2) * 64 + 2 * (kw & 3); }
 
 // two 4-column TMEM loads (two accumulators), one wait
 __device__ __forceinline__ void ld4x2(uint32_t t0, uint32_t t1, float a[4], float b[4]) {
@@ -578,23 +582,26 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         // ---- MMA 1: own values at all points, neighbours' traces ----------------------------------
         // D = A x [phi_hi, phi_hi] + A x [phi_lo, 0] = (x_hi + x_lo) phi_hi + x_hi phi_lo
         if (ct == 0) {
+            // descriptors advance by whole 16-byte units: a K step (256 B) adds 16, an 8-row group
+            // of a K1 operand ((K1/8) * 128 B) adds K1
+            constexpr uint64_t KSTEP = 16, RGRP = K1;
             const uint32_t id1 = tc::idesc_f16(64, N1), idn = tc::idesc_f16(64, NN);
+            const uint64_t dA1 = tc::kdesc(sA1, 0, K1), dAN = tc::kdesc(sAN, 0, K1);
+            const uint64_t dT1[2] = {tc::kdesc(sT1a, 0, K1), tc::kdesc(sT1b, 0, K1)};
 #pragma unroll
             for (int h = 0; h < 2; ++h)
 #pragma unroll
                 for (int ks = 0; ks < K1 / 16; ++ks)
-                    tc::mma(tmem + S::C_D1, tc::kdesc(sA1, ks, K1), tc::kdesc(h ? sT1b : sT1a, ks, K1), id1,
-                            (h | ks) != 0);
+                    tc::mma(tmem + S::C_D1, dA1 + KSTEP * ks, dT1[h] + KSTEP * ks, id1, (h | ks) != 0);
             for (int b = 0; b < nblk; ++b) {
                 const int d = sHdr[3 + b];
-                const __half* Ab = sAN + tc::kmajor((d >> 2) & 1023, 0, K1);   // first row: a multiple of 8
-                const int toff = tc::kmajor(FPAD * (d & 3), 0, K1);            // face slice of table 1
+                const uint64_t da = dAN + RGRP * (uint64_t)(((d >> 2) & 1023) >> 3);   // first row: a multiple of 8
+                const uint64_t toff = RGRP * (uint64_t)(FPAD / 8 * (d & 3));           // face slice of table 1
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
 #pragma unroll
                     for (int ks = 0; ks < K1 / 16; ++ks)
-                        tc::mma(tmem + S::C_DN + b * NN, tc::kdesc(Ab, ks, K1), tc::kdesc((h ? sT1b : sT1a) + toff, ks, K1),
-                                idn, (h | ks) != 0);
+                        tc::mma(tmem + S::C_DN + b * NN, da + KSTEP * ks, dT1[h] + toff + KSTEP * ks, idn, (h | ks) != 0);
             }
             tc::commit(mbar);
         }
@@ -705,11 +712,15 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                     const float* el = sEl + e * ELW;
                     float G[3][5];
                     contravariant(U, el + 9, gamma, G);
+                    int rp[5];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k)
+                    for (int v = 0; v < 5; ++v) rp[v] = rowpart(e * 5 + v, K2);
 #pragma unroll
-                        for (int v = 0; v < 5; ++v)
-                            *opword(sA2, e * 5 + v, k * NQ + q, K2) = split_pair(G[k][v] - el[18 + 5 * k + v]);
+                    for (int k = 0; k < 3; ++k) {
+                        uint32_t* A2k = reinterpret_cast<uint32_t*>(sA2 + kpart(k * NQ + q));
+#pragma unroll
+                        for (int v = 0; v < 5; ++v) A2k[rp[v] >> 1] = split_pair(G[k][v] - el[18 + 5 * k + v]);
+                    }
                 } else {
                     const int j = i - NV;
                     const int w = j / NQF, q = j - w * NQF;
@@ -741,16 +752,18 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                                                    : rusanov_f32(Um, Up, nv, gamma, H);
                     if (!ok) atomicOr(a.status, 1u);
                     const float* fb = sFbn + s * 5;
+                    {
+                        uint32_t* A2k = reinterpret_cast<uint32_t*>(sA2 + kpart(3 * NQ + f * NQF + q));
 #pragma unroll
-                    for (int v = 0; v < 5; ++v)
-                        *opword(sA2, e * 5 + v, 3 * NQ + f * NQF + q, K2) = split_pair(fmaf(geo.w, H[v], -fb[v]));
+                        for (int v = 0; v < 5; ++v) A2k[rowpart(e * 5 + v, K2) >> 1] = split_pair(fmaf(geo.w, H[v], -fb[v]));
+                    }
                     if (kind == SK_OWN) {
                         const float scp = sGeo[sp].w;
                         const float* fbp = sFbn + sp * 5;
                         const int ep = sp >> 2, fp = sp & 3;
+                        uint32_t* A2k = reinterpret_cast<uint32_t*>(sA2 + kpart(3 * NQ + fp * NQF + pq));
 #pragma unroll
-                        for (int v = 0; v < 5; ++v)
-                            *opword(sA2, ep * 5 + v, 3 * NQ + fp * NQF + pq, K2) = split_pair(-fmaf(scp, H[v], fbp[v]));
+                        for (int v = 0; v < 5; ++v) A2k[rowpart(ep * 5 + v, K2) >> 1] = split_pair(-fmaf(scp, H[v], fbp[v]));
                     }
                 }
             }
@@ -761,15 +774,16 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         tc::fence_after();
         // ---- MMA 2: projection onto the weighted basis gradients + face lift ----------------------
         if (ct == 0) {
+            constexpr uint64_t KSTEP = 16;
             const uint32_t id2 = tc::idesc_f16(64, N2);
+            const uint64_t dA2 = tc::kdesc(sA2, 0, K2), dTa = tc::kdesc(sT2a, 0, K2), dTb = tc::kdesc(sT2b, 0, K2);
             constexpr int KS = K2 / 16, KH = KS / 2;
-#pragma unroll 1
-            for (int ks = 0; ks < KS; ++ks) {
-                const int acc = ks < KH ? 0 : 1;
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
-                    tc::mma(tmem + S::C_D2 + acc * N2, tc::kdesc(sA2, ks, K2), tc::kdesc(h ? sT2b : sT2a, ks, K2),
-                            id2, (h != 0 || (ks != 0 && ks != KH)) ? 1u : 0u);
+            for (int ks = 0; ks < KS; ++ks) {
+                const uint32_t dcol = tmem + S::C_D2 + (ks < KH ? 0 : N2);
+                const uint32_t first = (ks == 0 || ks == KH) ? 0u : 1u;
+                tc::mma(dcol, dA2 + KSTEP * ks, dTa + KSTEP * ks, id2, first);
+                tc::mma(dcol, dA2 + KSTEP * ks, dTb + KSTEP * ks, id2, 1u);
             }
             tc::commit(mbar);
         }
@@ -994,8 +1008,13 @@ void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vect
                 cross[fc & 3].push_back(s);
             }
             slot[(size_t)t * SLOTS + s] = code;
-            if ((code & 3) != SK_SKIP) lists[(size_t)t * 2 * SLOTS + SLOTS + nw++] = (uint8_t)s;
         }
+        // work list grouped by kind (in-tile faces evaluated here, faces to other tiles, boundary
+        // faces), so that the warps of the flux phase mostly run one kind each
+        for (int kind : {(int)SK_OWN, (int)SK_CROSS, (int)SK_BND})
+            for (int s = 0; s < SLOTS; ++s)
+                if (t * ET + (s >> 2) < ne && (int)(slot[(size_t)t * SLOTS + s] & 3) == kind)
+                    lists[(size_t)t * 2 * SLOTS + SLOTS + nw++] = (uint8_t)s;
         int nc = 0, nb = 0, row = 0;
         int32_t* H = hdr.data() + (size_t)t * THDR;
         for (int fn = 0; fn < 4; ++fn)
