@@ -29,13 +29,13 @@
 // lower slot): both traces come from the tile's own MMA and the flux is
 // written to both sides.  Only faces to other tiles read the neighbour's
 // coefficients (from L2: consecutive elements of a space-filling-curve or RCM
-// order are spatial neighbours) for a trace MMA of their own.  Per tile:
-//   build    operand rows: own coefficients (modes 1..), neighbours in other
-//            tiles; per-element scaled J^-1 and mean-state fluxes;
-//   MMA 1    own values at the 4 Nqf face points and the Nq volume points,
-//            and the cross-tile neighbours' traces (blocks of one neighbour
-//            face: a 16-row slice of the face-point table); meanwhile the
-//            per-face normals and mean-state normal fluxes;
+// order are spatial neighbours); their traces are evaluated on the CUDA cores
+// in FP32 while the tensor cores work.  Per tile:
+//   build    operand rows of the own coefficients (modes 1..); the
+//            coefficient blocks of the neighbours in other tiles;
+//   MMA 1    own values at the 4 Nqf face points and the Nq volume points;
+//            meanwhile the neighbours' traces (FP32) and the per-element
+//            scaled J^-1 and mean-state fluxes;
 //   stage    TMEM -> shared memory (FP32 point states);
 //   flux     volume points: contravariant flux deviation; face points:
 //            Rusanov / Roe flux (ghost state on boundary faces) written to
@@ -62,7 +62,6 @@ constexpr int MT = 512;      // threads per CTA
 constexpr int CT = 256;      // threads per context
 constexpr int ET = 12;       // elements per tile
 constexpr int SLOTS = 4 * ET;
-constexpr int PB = 12;       // cross-tile face pairs per neighbour operand block (60 rows)
 constexpr int TMEM_COLS = 512, CTX_COLS = 256;
 constexpr long WAIT_ITERS = 20000000;
 
@@ -78,16 +77,11 @@ constexpr int a128(int x) { return (x + 127) / 128 * 128; }
 //   bits 2-8   partner slot (in-tile faces)
 //   bits 9-11  relative orientation (face-point permutation index)
 //   bits 12-18 cross index (faces to other tiles)
+//   bits 19-20 the neighbour's local face (faces to other tiles)
 //   bits 21-22 boundary type
-// Tile header (THDR ints): cross count, work count, number of neighbour blocks, then one word per
-// block: the neighbours' common local face (bits 0-1), first operand row (bits 2-11, a multiple
-// of 8), face pairs (bits 12-16), first cross index (bits 17-23).  Faces to other tiles are
-// ordered by the neighbour's local face, so that every block of neighbour rows multiplies one
-// 16-row slice of the face-point table.  Per cross index, the neighbour's element id.
+// Tile header (THDR ints): cross count, work count.  Per cross index, the neighbour's element id.
 enum { SK_OWN = 0, SK_SKIP = 1, SK_CROSS = 2, SK_BND = 3 };
-constexpr int THDR = 12;
-constexpr int MAXB = 7;       // neighbour blocks: sum over the 4 faces of ceil(pairs / PB) <= 4 + 3
-constexpr int ANR = 288;      // neighbour operand rows: 48 pairs x 5 + 8-row alignment of 7 blocks
+constexpr int THDR = 2;
 
 template <int P>
 struct SPlan {
@@ -99,18 +93,16 @@ struct SPlan {
     // operands hold interleaved split pairs: logical index k -> positions 2k (hi), 2k+1 (lo)
     static constexpr int K1 = r16(2 * NB);        // modes
     static constexpr int N1 = r8(NPT);            // M = 64 MMAs take N in steps of 8
-    static constexpr int NN = 16;                 // neighbour traces: a 16-row slice of the same table
+    static constexpr int NV5 = 5 * NB;            // coefficients per element
     static constexpr int KL2 = 3 * NQ + NF;       // logical (k, q) then (f, q)
     static constexpr int K2 = r16(2 * KL2);
     static constexpr int N2 = r8(NB);
     static constexpr int NCH = (NB + 3) / 4;      // 4-mode chunks
     // f16 table images in global memory (halves): T1 a|b, T2 a|b
     static constexpr int G_T1 = 0, G_T2 = 2 * N1 * K1, TAB_HALVES = G_T2 + 2 * N2 * K2;
-    // tensor memory of a context: D1 (own points), DN[MAXB] (neighbour traces), D2[2] (projection,
-    // two K halves)
-    static constexpr int C_D1 = 0, C_DN = r16(N1), C_D2 = C_DN + MAXB * NN;
+    // tensor memory of a context: D1 (own points), D2[2] (projection, two K halves)
+    static constexpr int C_D1 = 0, C_D2 = r16(N1);
     static_assert(C_D2 + 2 * N2 <= CTX_COLS, "tensor memory");
-    static_assert(3 * FPAD + NN <= N1 + 8, "neighbour slice inside table 1");
     // point-state staging [ET][5][VSTR]: VSTR = 4 (mod 8) and >= the staged columns, so that the
     // 16-byte stores of 8 consecutive rows (5e + v) and the volume-point loads avoid bank conflicts
     static constexpr int SCOLS = (NPT + 7) / 8 * 8;
@@ -119,19 +111,22 @@ struct SPlan {
     static constexpr int ELW = 52;                // per element: I[9], Is[9], Gbar_s[15], Fbar[15], ts, inv2
     // shared memory (bytes): tables, then one region per context
     static constexpr int SZ_T1 = 2 * N1 * K1 * 2, SZ_T2 = 2 * N2 * K2 * 2;
-    static constexpr int SZ_A1 = 64 * K1 * 2, SZ_AN = ANR * K1 * 2, SZ_A2 = 64 * K2 * 2;
-    static constexpr int SZ_AU = (SZ_A1 + SZ_AN) > SZ_A2 ? (SZ_A1 + SZ_AN) : SZ_A2;
-    static constexpr int O_T1 = 0, O_T2 = a128(O_T1 + SZ_T1), O_CTX = a128(O_T2 + SZ_T2);
+    // operand union of a context: A1 and the neighbours' coefficient blocks (build .. MMA 1),
+    // then A2 (flux phase .. MMA 2)
+    static constexpr int SZ_A1 = 64 * K1 * 2, SZ_C = SLOTS * NV5 * 4, SZ_A2 = 64 * K2 * 2;
+    static constexpr int SZ_AU = (SZ_A1 + SZ_C) > SZ_A2 ? (SZ_A1 + SZ_C) : SZ_A2;
+    static constexpr int SZ_PF = 4 * NQF * NB * 4;                         // FP32 face-point basis [f][p][j]
+    static constexpr int O_T1 = 0, O_T2 = a128(O_T1 + SZ_T1), O_PF = a128(O_T2 + SZ_T2);
+    static constexpr int O_CTX = a128(O_PF + SZ_PF);
     // context-relative offsets
     static constexpr int X_AU = 0;
     static constexpr int X_SU = a128(X_AU + SZ_AU);                        // float [ET][5][VSTR]
     static constexpr int X_SN = a128(X_SU + ET * USTR * 4);                // float [SLOTS][5][NQF4]
-    static constexpr int X_ROW = a128(X_SN + SLOTS * 5 * NQF4 * 4);       // float2 [64 + ANR] (mean, factor)
-    static constexpr int X_GEO = a128(X_ROW + (64 + ANR) * 8);            // float4 [SLOTS] (n, sc)
+    static constexpr int X_ROW = a128(X_SN + SLOTS * 5 * NQF4 * 4);       // float2 [64] (mean, factor)
+    static constexpr int X_GEO = a128(X_ROW + 64 * 8);                    // float4 [SLOTS] (n, sc)
     static constexpr int X_FBN = a128(X_GEO + SLOTS * 16);                // float [SLOTS][5]
     static constexpr int X_EL = a128(X_FBN + SLOTS * 5 * 4);              // float [ET][ELW]
-    static constexpr int X_HDR = a128(X_EL + ET * ELW * 4);               // int [THDR]
-    static constexpr int X_CODE = X_HDR + THDR * 4;                        // uint32 [SLOTS]
+    static constexpr int X_CODE = a128(X_EL + ET * ELW * 4);              // uint32 [SLOTS]
     static constexpr int X_LIST = X_CODE + SLOTS * 4;                      // uint8 [2*SLOTS]: cross, work
     static constexpr int X_MB = a128(X_LIST + 2 * SLOTS);                  // mbarrier
     static constexpr int CTX_BYTES = a128(X_MB + 16);
@@ -139,8 +134,6 @@ struct SPlan {
     static constexpr int O_SLOT = a128(O_PERM + 6 * NQF);                  // tmem slot
     static constexpr int BYTES = O_SLOT + 16;
     static_assert(BYTES <= 227 * 1024, "shared memory");
-    // the last neighbour block's MMA reads up to 63 rows past its own: inside the context's staging
-    static_assert(SZ_A1 + (ANR + 64) * K1 * 2 <= X_SN, "neighbour operand overrun");
 };
 
 struct StageArgs {
@@ -157,6 +150,7 @@ struct StageArgs {
     const int32_t* xnbr;    // [ntiles][SLOTS] neighbour element of each cross index
     const int8_t* fperm;    // [6][Nqf]
     const uint16_t* tab16;  // f16 table images
+    const float* phif;      // FP32 face-point basis [4][Nb][Nqf] (phi_j at point q of local face f)
     int64_t ne;
     int mode;               // 0 residual, 1 RK stage
     float a, bdt;           // RK: out = U + a (U0 - U) + b dt R  (a + b = 1)
@@ -384,11 +378,8 @@ __device__ __forceinline__ void zero_row(__half* A, int r, int K1) {
     for (int ch = 0; ch < K1 / 8; ++ch) *reinterpret_cast<uint4*>(A + tc::kmajor(r, 8 * ch, K1)) = make_uint4(0, 0, 0, 0);
 }
 
-// 32-bit word (split pair of logical K index kw) of row r of a K-major operand with K halves
-__device__ __forceinline__ uint32_t* opword(__half* A, int r, int kw, int K) {
-    return reinterpret_cast<uint32_t*>(A + tc::kmajor(r, 2 * kw, K));
-}
-// the same word split into a row part and a K part of the half index: kmajor(r, 2 kw, K) =
+// half index of the 32-bit word holding the split pair of logical K index kw in row r of a
+// K-major operand with K halves, split into a row part and a K part: kmajor(r, 2 kw, K) =
 // rowpart(r, K) + kpart(kw)
 __host__ __device__ constexpr int rowpart(int r, int K) { return (r >> 3) * (K >> 3) * 64 + (r & 7) * 8; }
 __device__ __forceinline__ int kpart(int kw) { return (kw >> 2) * 64 + 2 * (kw & 3); }
@@ -460,7 +451,7 @@ template <int P, int FLUX>
 __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     using S = SPlan<P>;
     constexpr int NB = S::NB, NQ = S::NQ, NQF = S::NQF, NQ4 = S::NQ4, NQF4 = S::NQF4, FPAD = S::FPAD;
-    constexpr int K1 = S::K1, K2 = S::K2, N1 = S::N1, NN = S::NN, N2 = S::N2, VSTR = S::VSTR, USTR = S::USTR;
+    constexpr int K1 = S::K1, K2 = S::K2, N1 = S::N1, N2 = S::N2, VSTR = S::VSTR, USTR = S::USTR, NV5 = S::NV5;
     constexpr int ELW = S::ELW;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -472,15 +463,15 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     const __half* sT2b = sT2a + N2 * K2;
     unsigned char* cx = smem + S::O_CTX + ctx * S::CTX_BYTES;
     __half* sA1 = reinterpret_cast<__half*>(cx + S::X_AU);
-    __half* sAN = reinterpret_cast<__half*>(cx + S::X_AU + S::SZ_A1);
+    float* sC = reinterpret_cast<float*>(cx + S::X_AU + S::SZ_A1);   // neighbour coefficient blocks
     __half* sA2 = reinterpret_cast<__half*>(cx + S::X_AU);
+    const float* sPhiF = reinterpret_cast<const float*>(smem + S::O_PF);
     float* sU = reinterpret_cast<float*>(cx + S::X_SU);
     float* sN = reinterpret_cast<float*>(cx + S::X_SN);
     float2* sRow = reinterpret_cast<float2*>(cx + S::X_ROW);
     float4* sGeo = reinterpret_cast<float4*>(cx + S::X_GEO);
     float* sFbn = reinterpret_cast<float*>(cx + S::X_FBN);
     float* sEl = reinterpret_cast<float*>(cx + S::X_EL);
-    int* sHdr = reinterpret_cast<int*>(cx + S::X_HDR);
     uint32_t* sCode = reinterpret_cast<uint32_t*>(cx + S::X_CODE);
     uint8_t* sList = reinterpret_cast<uint8_t*>(cx + S::X_LIST);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(cx + S::X_MB);
@@ -501,6 +492,12 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         for (int i = tid; i < 2 * S::CTX_BYTES / 16; i += MT) z[i] = make_uint4(0, 0, 0, 0);
         int8_t* pm = reinterpret_cast<int8_t*>(smem + S::O_PERM);
         for (int i = tid; i < 6 * NQF; i += MT) pm[i] = a.fperm[i];
+        // face-point basis, transposed to [f][p][j] so a point's row is contiguous
+        float* pf = reinterpret_cast<float*>(smem + S::O_PF);
+        for (int i = tid; i < 4 * NQF * NB; i += MT) {
+            const int f = i / (NQF * NB), p = (i / NB) % NQF, j = i % NB;
+            pf[i] = a.phif[(f * NB + j) * NQF + p];
+        }
     }
     __syncthreads();
     if (ct == 0) tc::mbar_init(mbar);
@@ -523,7 +520,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         const int64_t e0 = tile * ET;
         const int nel = (a.ne - e0) < (int64_t)ET ? (int)(a.ne - e0) : ET;
         const int32_t* hdr = a.thdr + tile * THDR;
-        const int ncross = __ldg(hdr), nwork = __ldg(hdr + 1), nblk = __ldg(hdr + 2);
+        const int ncross = __ldg(hdr), nwork = __ldg(hdr + 1);
         // ---- L2 prefetch of this context's next tile (contiguous blocks) ---------------------------
         if (ct == 0) {
             const int64_t nt = tile + tstride;
@@ -559,20 +556,18 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
             sCode[t2] = __ldg(a.slot + tile * SLOTS + t2);
             sList[t2] = __ldg(tl + t2);
             sList[SLOTS + t2] = __ldg(tl + SLOTS + t2);
-            if (t2 < THDR) sHdr[t2] = __ldg(hdr + t2);
         } else if (ct >= 128) {
-            // neighbour operand rows of the faces to other tiles, grouped in blocks of one
-            // neighbour face: row R_b + 5 i + v for the i-th pair of block b
-            for (int rr = ct - 128; rr < 5 * ncross; rr += CT - 128) {
-                const int c = rr / 5, v = rr - 5 * c;
+            // coefficient blocks (hi plane) of the neighbours in other tiles, by cross index
+            constexpr int VW = NV5 % 4 == 0 ? 4 : 2;   // 16- or 8-byte units (element blocks are aligned)
+            constexpr int NU = NV5 / VW;
+            for (int i = ct - 128; i < ncross * NU; i += CT - 128) {
+                const int c = i / NU, u = i - c * NU;
                 const int64_t n = __ldg(a.xnbr + tile * SLOTS + c);
-                int row = 0;
-                for (int b = 0; b < nblk; ++b) {
-                    const int d = __ldg(hdr + 3 + b);
-                    const int cs = (d >> 17) & 127, np = (d >> 12) & 31;
-                    if (c >= cs && c < cs + np) row = ((d >> 2) & 1023) + 5 * (c - cs) + v;
-                }
-                sRow[64 + row] = build_row<P>(a.U_hi + (n * 5 + v) * NB, sAN, row, a.inv_beta1);
+                const float* src = a.U_hi + n * NV5 + u * VW;
+                if constexpr (VW == 4)
+                    *reinterpret_cast<float4*>(sC + c * NV5 + 4 * u) = __ldg(reinterpret_cast<const float4*>(src));
+                else
+                    *reinterpret_cast<float2*>(sC + c * NV5 + 2 * u) = __ldg(reinterpret_cast<const float2*>(src));
             }
         }
         tc::fence_async_smem();
@@ -582,28 +577,35 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         // ---- MMA 1: own values at all points, neighbours' traces ----------------------------------
         // D = A x [phi_hi, phi_hi] + A x [phi_lo, 0] = (x_hi + x_lo) phi_hi + x_hi phi_lo
         if (ct == 0) {
-            // descriptors advance by whole 16-byte units: a K step (256 B) adds 16, an 8-row group
-            // of a K1 operand ((K1/8) * 128 B) adds K1
-            constexpr uint64_t KSTEP = 16, RGRP = K1;
-            const uint32_t id1 = tc::idesc_f16(64, N1), idn = tc::idesc_f16(64, NN);
-            const uint64_t dA1 = tc::kdesc(sA1, 0, K1), dAN = tc::kdesc(sAN, 0, K1);
+            // descriptors advance by whole 16-byte units: a K step (256 B) adds 16
+            constexpr uint64_t KSTEP = 16;
+            const uint32_t id1 = tc::idesc_f16(64, N1);
+            const uint64_t dA1 = tc::kdesc(sA1, 0, K1);
             const uint64_t dT1[2] = {tc::kdesc(sT1a, 0, K1), tc::kdesc(sT1b, 0, K1)};
 #pragma unroll
             for (int h = 0; h < 2; ++h)
 #pragma unroll
                 for (int ks = 0; ks < K1 / 16; ++ks)
                     tc::mma(tmem + S::C_D1, dA1 + KSTEP * ks, dT1[h] + KSTEP * ks, id1, (h | ks) != 0);
-            for (int b = 0; b < nblk; ++b) {
-                const int d = sHdr[3 + b];
-                const uint64_t da = dAN + RGRP * (uint64_t)(((d >> 2) & 1023) >> 3);   // first row: a multiple of 8
-                const uint64_t toff = RGRP * (uint64_t)(FPAD / 8 * (d & 3));           // face slice of table 1
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int ks = 0; ks < K1 / 16; ++ks)
-                        tc::mma(tmem + S::C_DN + b * NN, da + KSTEP * ks, dT1[h] + toff + KSTEP * ks, idn, (h | ks) != 0);
-            }
             tc::commit(mbar);
+        }
+        // the neighbours' traces at their face points (FP32, own point order of the neighbour's
+        // face), while the tensor cores work: thread per (cross index, point)
+        for (int i = ct; i < ncross * NQF; i += CT) {
+            const int c = i / NQF, p = i - c * NQF;
+            const int fn = (sCode[sList[c]] >> 19) & 3;
+            const float* ph = sPhiF + (fn * NQF + p) * NB;
+            const float* cf = sC + c * NV5;
+            float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                const float w = ph[j];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) acc[v] = fmaf(cf[v * NB + j], w, acc[v]);
+            }
+            float* nd = sN + c * 5 * NQF4 + p;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) nd[v * NQF4] = acc[v];
         }
         // per element while the tensor cores work (used by the faces below and the flux phase)
         if (ct >= 64 && ct < 64 + ET) {
@@ -674,21 +676,6 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                     for (int t = 0; t < 8; ++t) val[t] = fmaf(val[t], mr.y, mr.x);
                     *reinterpret_cast<float4*>(dst + 8 * ch) = make_float4(val[0], val[1], val[2], val[3]);
                     *reinterpret_cast<float4*>(dst + 8 * ch + 4) = make_float4(val[4], val[5], val[6], val[7]);
-                }
-            }
-            for (int b = part; b < nblk; b += 2) {
-                const int d = sHdr[3 + b];
-                const int R0 = (d >> 2) & 1023, npair = (d >> 12) & 31, cs = (d >> 17) & 127;
-                float val[16];
-                tc::ld16(tmem + lane_base + S::C_DN + b * NN, val);
-                if (has_row && lrow < 5 * npair) {
-                    const float2 nr = sRow[64 + R0 + lrow];
-                    float* nd = sN + ((cs + lrow / 5) * 5 + v) * NQF4;
-#pragma unroll
-                    for (int t = 0; t < NQF4; t += 4)
-                        *reinterpret_cast<float4*>(nd + t) =
-                            make_float4(fmaf(val[t], nr.y, nr.x), fmaf(val[t + 1], nr.y, nr.x),
-                                        fmaf(val[t + 2], nr.y, nr.x), fmaf(val[t + 3], nr.y, nr.x));
                 }
             }
         }
@@ -978,9 +965,9 @@ void build_mixed_tables(int p, const RefData& ref, std::vector<uint16_t>& out, f
 }
 
 // Tile metadata of the fused kernel (host, once per mesh): for every tile of ET consecutive
-// internal elements, the slot codes, the list of faces to other tiles (ordered by the neighbour's
-// local face; cross index = position in this list), the list of faces whose flux the tile
-// evaluates (work list), and the tile header (counts and neighbour operand blocks).
+// internal elements, the slot codes, the list of faces to other tiles (cross index = position in
+// this list) with the neighbours' element ids, the list of faces whose flux the tile evaluates
+// (work list), and the two counts.
 void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vector<uint8_t>& lists,
                        std::vector<int32_t>& hdr, std::vector<int32_t>& xnbr) {
     const int64_t ne = h.ne, ntiles = (ne + ET - 1) / ET;
@@ -989,7 +976,6 @@ void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vect
     hdr.assign((size_t)ntiles * THDR, 0);
     xnbr.assign((size_t)ntiles * SLOTS, 0);
     for (int64_t t = 0; t < ntiles; ++t) {
-        std::vector<int> cross[4];
         int nw = 0;
         for (int s = 0; s < SLOTS; ++s) {
             const int64_t e = t * ET + (s >> 2);
@@ -1004,8 +990,7 @@ void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vect
                 const int sp = (int)(n - t * ET) * 4 + (int)(fc & 3);
                 code = (sp > s ? SK_OWN : SK_SKIP) | ((uint32_t)sp << 2) | ((fc >> 2) << 9);
             } else {
-                code = SK_CROSS | ((fc >> 2) << 9);
-                cross[fc & 3].push_back(s);
+                code = SK_CROSS | ((fc >> 2) << 9) | ((fc & 3) << 19);
             }
             slot[(size_t)t * SLOTS + s] = code;
         }
@@ -1015,23 +1000,17 @@ void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vect
             for (int s = 0; s < SLOTS; ++s)
                 if (t * ET + (s >> 2) < ne && (int)(slot[(size_t)t * SLOTS + s] & 3) == kind)
                     lists[(size_t)t * 2 * SLOTS + SLOTS + nw++] = (uint8_t)s;
-        int nc = 0, nb = 0, row = 0;
+        // faces to other tiles: cross index in slot order
+        int nc = 0;
+        for (int s = 0; s < SLOTS; ++s) {
+            if (t * ET + (s >> 2) >= ne || (slot[(size_t)t * SLOTS + s] & 3) != SK_CROSS) continue;
+            slot[(size_t)t * SLOTS + s] |= (uint32_t)nc << 12;
+            xnbr[(size_t)t * SLOTS + nc] = h.nbr[(t * ET + (s >> 2)) * 4 + (s & 3)];
+            lists[(size_t)t * 2 * SLOTS + nc++] = (uint8_t)s;
+        }
         int32_t* H = hdr.data() + (size_t)t * THDR;
-        for (int fn = 0; fn < 4; ++fn)
-            for (size_t k0 = 0; k0 < cross[fn].size(); k0 += PB) {
-                const int np = (int)std::min<size_t>(PB, cross[fn].size() - k0);
-                H[3 + nb++] = fn | (row << 2) | (np << 12) | (nc << 17);
-                for (int k = 0; k < np; ++k) {
-                    const int s = cross[fn][k0 + k];
-                    slot[(size_t)t * SLOTS + s] |= (uint32_t)nc << 12;
-                    xnbr[(size_t)t * SLOTS + nc] = h.nbr[(t * ET + (s >> 2)) * 4 + (s & 3)];
-                    lists[(size_t)t * 2 * SLOTS + nc++] = (uint8_t)s;
-                }
-                row = (row + 5 * np + 7) / 8 * 8;
-            }
         H[0] = nc;
         H[1] = nw;
-        H[2] = nb;
     }
 }
 
@@ -1052,6 +1031,7 @@ cudaError_t launch_residual_mixed(dg_mesh* m, const float* U_hi, const float* U_
     r.xnbr = m->d_mxnbr;
     r.fperm = m->d_fperm;
     r.tab16 = m->d_tab16;
+    r.phif = static_cast<const float*>(m->d_tab) + TabLayout(m->p).phif;
     r.ne = m->host.ne;
     r.mode = mode;
     // RK stage out = ca U0 + cb (U + dt R) with ca + cb = 1, written as U + ca (U0 - U) + cb dt R
