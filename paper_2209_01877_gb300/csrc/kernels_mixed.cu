@@ -108,7 +108,8 @@ struct SPlan {
     static constexpr int SCOLS = (NPT + 7) / 8 * 8;
     static constexpr int VSTR = SCOLS + ((4 - SCOLS % 8) + 8) % 8;
     static constexpr int USTR = 5 * VSTR;
-    static constexpr int ELW = 52;                // per element: I[9], Is[9], Gbar_s[15], Fbar[15], ts, inv2
+    // per element: I[9], Is[9], Gbar_s[15], Fbar[15], ts, inv2, the A2 row parts of its 5 rows (int)
+    static constexpr int ELW = 56;
     // shared memory (bytes): tables, then one region per context
     static constexpr int SZ_T1 = 2 * N1 * K1 * 2, SZ_T2 = 2 * N2 * K2 * 2;
     // operand union of a context: A1 and the neighbours' coefficient blocks (build .. MMA 1),
@@ -123,9 +124,9 @@ struct SPlan {
     static constexpr int X_SU = a128(X_AU + SZ_AU);                        // float [ET][5][VSTR]
     static constexpr int X_SN = a128(X_SU + ET * USTR * 4);                // float [SLOTS][5][NQF4]
     static constexpr int X_ROW = a128(X_SN + SLOTS * 5 * NQF4 * 4);       // float2 [64] (mean, factor)
-    static constexpr int X_GEO = a128(X_ROW + 64 * 8);                    // float4 [SLOTS] (n, sc)
-    static constexpr int X_FBN = a128(X_GEO + SLOTS * 16);                // float [SLOTS][5]
-    static constexpr int X_EL = a128(X_FBN + SLOTS * 5 * 4);              // float [ET][ELW]
+    // per slot, 3 float4: (n, sc), (sc Fbar.n)[0..3], ((sc Fbar.n)[4], staging offset, first K word, -)
+    static constexpr int X_REC = a128(X_ROW + 64 * 8);
+    static constexpr int X_EL = a128(X_REC + SLOTS * 48);                 // float [ET][ELW]
     static constexpr int X_CODE = a128(X_EL + ET * ELW * 4);              // uint32 [SLOTS]
     static constexpr int X_LIST = X_CODE + SLOTS * 4;                      // uint8 [2*SLOTS]: cross, work
     static constexpr int X_MB = a128(X_LIST + 2 * SLOTS);                  // mbarrier
@@ -450,7 +451,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t& phase, int ct,
 template <int P, int FLUX>
 __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     using S = SPlan<P>;
-    constexpr int NB = S::NB, NQ = S::NQ, NQF = S::NQF, NQ4 = S::NQ4, NQF4 = S::NQF4, FPAD = S::FPAD;
+    constexpr int NB = S::NB, NQ = S::NQ, NQF = S::NQF, NQF4 = S::NQF4, FPAD = S::FPAD;
     constexpr int K1 = S::K1, K2 = S::K2, N1 = S::N1, N2 = S::N2, VSTR = S::VSTR, USTR = S::USTR, NV5 = S::NV5;
     constexpr int ELW = S::ELW;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -469,8 +470,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     float* sU = reinterpret_cast<float*>(cx + S::X_SU);
     float* sN = reinterpret_cast<float*>(cx + S::X_SN);
     float2* sRow = reinterpret_cast<float2*>(cx + S::X_ROW);
-    float4* sGeo = reinterpret_cast<float4*>(cx + S::X_GEO);
-    float* sFbn = reinterpret_cast<float*>(cx + S::X_FBN);
+    float4* sRec = reinterpret_cast<float4*>(cx + S::X_REC);
     float* sEl = reinterpret_cast<float*>(cx + S::X_EL);
     uint32_t* sCode = reinterpret_cast<uint32_t*>(cx + S::X_CODE);
     uint8_t* sList = reinterpret_cast<uint8_t*>(cx + S::X_LIST);
@@ -638,6 +638,8 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                     }
                 el[48] = ts;
                 el[49] = a.inv_beta2 * __fdividef(1.f, ts);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) el[50 + v] = __int_as_float(rowpart(e * 5 + v, K2));
             }
         }
         if (!tc_wait(mbar, phase, ct, bar_id)) {
@@ -656,10 +658,14 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 const float isf = rsqrtf(g0 * g0 + g1 * g1 + g2 * g2);
                 const float n0 = -g0 * isf, n1 = -g1 * isf, n2 = -g2 * isf;
                 const float sc = -el[48] * __fdividef(1.f, isf);
-                sGeo[s] = make_float4(n0, n1, n2, sc);
                 const float* F = el + 33;
+                float fb[5];
 #pragma unroll
-                for (int v = 0; v < 5; ++v) sFbn[s * 5 + v] = sc * (F[v] * n0 + F[5 + v] * n1 + F[10 + v] * n2);
+                for (int v = 0; v < 5; ++v) fb[v] = sc * (F[v] * n0 + F[5 + v] * n1 + F[10 + v] * n2);
+                sRec[3 * s] = make_float4(n0, n1, n2, sc);
+                sRec[3 * s + 1] = make_float4(fb[0], fb[1], fb[2], fb[3]);
+                sRec[3 * s + 2] = make_float4(fb[4], __int_as_float(e * USTR + FPAD * f),
+                                              __int_as_float(3 * NQ + f * NQF), 0.f);
             }
         }
         // ---- stage TMEM -> shared memory: point states (mean + deviation x factor) ----------------
@@ -683,15 +689,15 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         ctx_sync(bar_id);
         // ---- fluxes -> operand A2 (row (e, v); K: volume (k, q), then face (f, q)) ---------------
         {
-            // volume items: lanes = 8 elements x 4 consecutive points (conflict-free 32-bit
-            // operand stores), two element groups (the second half full)
-            constexpr int NV = NQ4 * 16;
+            // volume items: lanes = 4 elements x 8 consecutive points, 3 element groups
+            constexpr int NQ8 = (NQ + 7) / 8 * 8;
+            constexpr int NV = NQ8 * ET;
             const int nitems = NV + nwork * NQF;
             for (int i = ct; i < nitems; i += CT) {
                 if (i < NV) {
                     const int wi = i >> 5, ln = i & 31;
-                    const int g = wi >> 1, eb = wi & 1;
-                    const int e = eb * 8 + (ln >> 2), q = g * 4 + (ln & 3);
+                    const int g = wi / (ET / 4), eb = wi - g * (ET / 4);
+                    const int e = eb * 4 + (ln >> 3), q = g * 8 + (ln & 7);
                     if (e >= nel || q >= NQ) continue;
                     const float* u = sU + e * USTR + 4 * FPAD + q;
                     const float U[5] = {u[0], u[VSTR], u[2 * VSTR], u[3 * VSTR], u[4 * VSTR]};
@@ -701,7 +707,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                     contravariant(U, el + 9, gamma, G);
                     int rp[5];
 #pragma unroll
-                    for (int v = 0; v < 5; ++v) rp[v] = rowpart(e * 5 + v, K2);
+                    for (int v = 0; v < 5; ++v) rp[v] = __float_as_int(el[50 + v]);
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         uint32_t* A2k = reinterpret_cast<uint32_t*>(sA2 + kpart(k * NQ + q));
@@ -713,16 +719,16 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                     const int w = j / NQF, q = j - w * NQF;
                     const int s = sList[SLOTS + w];
                     const uint32_t code = sCode[s];
-                    const int kind = code & 3, e = s >> 2, f = s & 3;
-                    const float* um = sU + e * USTR + FPAD * f + q;
+                    const int kind = code & 3, e = s >> 2;
+                    const float4 r0 = sRec[3 * s], r1 = sRec[3 * s + 1], r2 = sRec[3 * s + 2];
+                    const float* um = sU + __float_as_int(r2.y) + q;
                     const float Um[5] = {um[0], um[VSTR], um[2 * VSTR], um[3 * VSTR], um[4 * VSTR]};
-                    const float4 geo = sGeo[s];
-                    const float nv[3] = {geo.x, geo.y, geo.z};
+                    const float nv[3] = {r0.x, r0.y, r0.z};
                     const int pq = sPerm[((code >> 9) & 7) * NQF + q];
                     const int sp = (code >> 2) & 127;
                     float Up[5];
                     if (kind == SK_OWN) {
-                        const float* up = sU + (sp >> 2) * USTR + FPAD * (sp & 3) + pq;
+                        const float* up = sU + __float_as_int(sRec[3 * sp + 2].y) + pq;
 #pragma unroll
                         for (int v = 0; v < 5; ++v) Up[v] = up[v * VSTR];
                     } else if (kind == SK_CROSS) {
@@ -738,19 +744,22 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                     const bool ok = FLUX == DG_ROE ? roe_f32(Um, Up, nv, gamma, a.roe_eps, H)
                                                    : rusanov_f32(Um, Up, nv, gamma, H);
                     if (!ok) atomicOr(a.status, 1u);
-                    const float* fb = sFbn + s * 5;
                     {
-                        uint32_t* A2k = reinterpret_cast<uint32_t*>(sA2 + kpart(3 * NQ + f * NQF + q));
+                        const float fb[5] = {r1.x, r1.y, r1.z, r1.w, r2.x};
+                        const float* el = sEl + e * ELW;
+                        uint32_t* A2k = reinterpret_cast<uint32_t*>(sA2 + kpart(__float_as_int(r2.z) + q));
 #pragma unroll
-                        for (int v = 0; v < 5; ++v) A2k[rowpart(e * 5 + v, K2) >> 1] = split_pair(fmaf(geo.w, H[v], -fb[v]));
+                        for (int v = 0; v < 5; ++v)
+                            A2k[__float_as_int(el[50 + v]) >> 1] = split_pair(fmaf(r0.w, H[v], -fb[v]));
                     }
                     if (kind == SK_OWN) {
-                        const float scp = sGeo[sp].w;
-                        const float* fbp = sFbn + sp * 5;
-                        const int ep = sp >> 2, fp = sp & 3;
-                        uint32_t* A2k = reinterpret_cast<uint32_t*>(sA2 + kpart(3 * NQ + fp * NQF + pq));
+                        const float4 p0 = sRec[3 * sp], p1 = sRec[3 * sp + 1], p2 = sRec[3 * sp + 2];
+                        const float fbp[5] = {p1.x, p1.y, p1.z, p1.w, p2.x};
+                        const float* elp = sEl + (sp >> 2) * ELW;
+                        uint32_t* A2k = reinterpret_cast<uint32_t*>(sA2 + kpart(__float_as_int(p2.z) + pq));
 #pragma unroll
-                        for (int v = 0; v < 5; ++v) A2k[rowpart(ep * 5 + v, K2) >> 1] = split_pair(-fmaf(scp, H[v], fbp[v]));
+                        for (int v = 0; v < 5; ++v)
+                            A2k[__float_as_int(elp[50 + v]) >> 1] = split_pair(-fmaf(p0.w, H[v], fbp[v]));
                     }
                 }
             }
