@@ -112,10 +112,9 @@ struct SPlan {
     static constexpr int ELW = 56;
     // shared memory (bytes): tables, then one region per context
     static constexpr int SZ_T1 = 2 * N1 * K1 * 2, SZ_T2 = 2 * N2 * K2 * 2;
-    // operand union of a context: A1 and the neighbours' coefficient blocks (build .. MMA 1),
-    // then A2 (flux phase .. MMA 2)
+    // operand union of a context: A1 (build .. MMA 1), then A2 (flux phase .. MMA 2)
     static constexpr int SZ_A1 = 64 * K1 * 2, SZ_C = SLOTS * NV5 * 4, SZ_A2 = 64 * K2 * 2;
-    static constexpr int SZ_AU = (SZ_A1 + SZ_C) > SZ_A2 ? (SZ_A1 + SZ_C) : SZ_A2;
+    static constexpr int SZ_AU = SZ_A1 > SZ_A2 ? SZ_A1 : SZ_A2;
     static constexpr int SZ_PF = 4 * NQF * NB * 4;                         // FP32 face-point basis [f][p][j]
     static constexpr int O_T1 = 0, O_T2 = a128(O_T1 + SZ_T1), O_PF = a128(O_T2 + SZ_T2);
     static constexpr int O_CTX = a128(O_PF + SZ_PF);
@@ -129,7 +128,8 @@ struct SPlan {
     static constexpr int X_EL = a128(X_REC + SLOTS * 48);                 // float [ET][ELW]
     static constexpr int X_CODE = a128(X_EL + ET * ELW * 4);              // uint32 [SLOTS]
     static constexpr int X_LIST = X_CODE + SLOTS * 4;                      // uint8 [2*SLOTS]: cross, work
-    static constexpr int X_MB = a128(X_LIST + 2 * SLOTS);                  // mbarrier
+    static constexpr int X_C = a128(X_LIST + 2 * SLOTS);                   // float [SLOTS][5 Nb] neighbour blocks
+    static constexpr int X_MB = a128(X_C + SZ_C);                          // mbarrier
     static constexpr int CTX_BYTES = a128(X_MB + 16);
     static constexpr int O_PERM = O_CTX + 2 * CTX_BYTES;                   // int8 [6][NQF]
     static constexpr int O_SLOT = a128(O_PERM + 6 * NQF);                  // tmem slot
@@ -448,6 +448,28 @@ __device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t& phase, int ct,
 
 }  // namespace
 
+// asynchronous 8-byte global -> shared copy
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tc::smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+
+// asynchronous copies of a tile's neighbour coefficient blocks (hi plane) into sC, by cross
+// index; issued by the context's threads 128..255, awaited by the same threads
+template <int NV5>
+__device__ __forceinline__ void issue_neighbour_blocks(const StageArgs& a, int64_t tile, int ct, float* sC) {
+    constexpr int VW = NV5 % 4 == 0 ? 4 : 2;   // 16- or 8-byte units (element blocks are aligned)
+    constexpr int NU = NV5 / VW;
+    const int ncross = __ldg(a.thdr + tile * THDR);
+    for (int i = ct - 128; i < ncross * NU; i += CT - 128) {
+        const int c = i / NU, u = i - c * NU;
+        const int64_t n = __ldg(a.xnbr + tile * SLOTS + c);
+        const float* src = a.U_hi + n * NV5 + u * VW;
+        if constexpr (VW == 4) tc::cp_async16(sC + c * NV5 + 4 * u, src);
+        else cp_async8(sC + c * NV5 + 2 * u, src);
+    }
+    tc::cp_async_commit();
+}
+
 template <int P, int FLUX>
 __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     using S = SPlan<P>;
@@ -464,7 +486,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     const __half* sT2b = sT2a + N2 * K2;
     unsigned char* cx = smem + S::O_CTX + ctx * S::CTX_BYTES;
     __half* sA1 = reinterpret_cast<__half*>(cx + S::X_AU);
-    float* sC = reinterpret_cast<float*>(cx + S::X_AU + S::SZ_A1);   // neighbour coefficient blocks
+    float* sC = reinterpret_cast<float*>(cx + S::X_C);   // neighbour coefficient blocks (next tile's in flight)
     __half* sA2 = reinterpret_cast<__half*>(cx + S::X_AU);
     const float* sPhiF = reinterpret_cast<const float*>(smem + S::O_PF);
     float* sU = reinterpret_cast<float*>(cx + S::X_SU);
@@ -516,6 +538,9 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
 
     const int64_t ntiles = (a.ne + ET - 1) / ET;
     const int64_t tstride = 2 * (int64_t)gridDim.x;
+    // the first tile's neighbour blocks; later tiles' are issued one tile ahead, during MMA 2
+    if (ct >= 128 && 2 * (int64_t)blockIdx.x + ctx < ntiles)
+        issue_neighbour_blocks<NV5>(a, 2 * (int64_t)blockIdx.x + ctx, ct, sC);
     for (int64_t tile = 2 * (int64_t)blockIdx.x + ctx; tile < ntiles; tile += tstride) {
         const int64_t e0 = tile * ET;
         const int nel = (a.ne - e0) < (int64_t)ET ? (int)(a.ne - e0) : ET;
@@ -557,18 +582,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
             sList[t2] = __ldg(tl + t2);
             sList[SLOTS + t2] = __ldg(tl + SLOTS + t2);
         } else if (ct >= 128) {
-            // coefficient blocks (hi plane) of the neighbours in other tiles, by cross index
-            constexpr int VW = NV5 % 4 == 0 ? 4 : 2;   // 16- or 8-byte units (element blocks are aligned)
-            constexpr int NU = NV5 / VW;
-            for (int i = ct - 128; i < ncross * NU; i += CT - 128) {
-                const int c = i / NU, u = i - c * NU;
-                const int64_t n = __ldg(a.xnbr + tile * SLOTS + c);
-                const float* src = a.U_hi + n * NV5 + u * VW;
-                if constexpr (VW == 4)
-                    *reinterpret_cast<float4*>(sC + c * NV5 + 4 * u) = __ldg(reinterpret_cast<const float4*>(src));
-                else
-                    *reinterpret_cast<float2*>(sC + c * NV5 + 2 * u) = __ldg(reinterpret_cast<const float2*>(src));
-            }
+            tc::cp_async_wait_all();   // this tile's neighbour blocks (issued a tile ahead) have landed
         }
         tc::fence_async_smem();
         tc::fence_before();
@@ -783,6 +797,8 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
             }
             tc::commit(mbar);
         }
+        // the next tile's neighbour blocks (sC is free: this tile's traces are done)
+        if (ct >= 128 && tile + tstride < ntiles) issue_neighbour_blocks<NV5>(a, tile + tstride, ct, sC);
         // epilogue operands in flight while the tensor cores work: 4-mode chunks of this thread's row
         constexpr int NCH = S::NCH;
         constexpr bool VEC = NB % 4 == 0;
@@ -872,6 +888,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         ctx_sync(bar_id);
         tc::fence_after();
     }
+    tc::cp_async_wait_all();   // no copy outlives the context (a timed-out loop may leave one)
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
