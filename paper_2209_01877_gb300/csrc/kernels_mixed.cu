@@ -97,7 +97,6 @@ struct SPlan {
     static constexpr int KL2 = 3 * NQ + NF;       // logical (k, q) then (f, q)
     static constexpr int K2 = r16(2 * KL2);
     static constexpr int N2 = r8(NB);
-    static constexpr int NCH = (NB + 3) / 4;      // 4-mode chunks
     // f16 table images in global memory (halves): T1 a|b, T2 a|b
     static constexpr int G_T1 = 0, G_T2 = 2 * N1 * K1, TAB_HALVES = G_T2 + 2 * N2 * K2;
     // tensor memory of a context: D1 (own points), D2[2] (projection, two K halves)
@@ -385,12 +384,27 @@ __device__ __forceinline__ void zero_row(__half* A, int r, int K1) {
 __host__ __device__ constexpr int rowpart(int r, int K) { return (r >> 3) * (K >> 3) * 64 + (r & 7) * 8; }
 __device__ __forceinline__ int kpart(int kw) { return (kw >> 2) * 64 + 2 * (kw & 3); }
 
-// two 4-column TMEM loads (two accumulators), one wait
-__device__ __forceinline__ void ld4x2(uint32_t t0, uint32_t t1, float a[4], float b[4]) {
+// 16-lane TMEM loads of an M = 64 accumulator (its rows occupy lanes 0-15 of each quarter).
+// Thread t of the warp receives rows t/4 and t/4 + 8 of the quarter's 16 rows:
+//   .16x256b.x1 (8 columns): v[0], v[1] = row t/4, columns 2(t%4), 2(t%4)+1; v[2], v[3] = row t/4+8
+//   .16x128b.x1 (4 columns): v[0] = row t/4, column t%4; v[1] = row t/4+8
+__device__ __forceinline__ void ld16x256(uint32_t taddr, float v[4]) {
+    uint32_t r[4];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+// the same 8 columns of two accumulators, one wait
+__device__ __forceinline__ void ld16x256x2(uint32_t t0, uint32_t t1, float a[4], float b[4]) {
     uint32_t r[8];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%8];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%9];\n"
+        "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%8];\n"
+        "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%4,%5,%6,%7}, [%9];\n"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
         : "r"(t0), "r"(t1)
@@ -401,6 +415,20 @@ __device__ __forceinline__ void ld4x2(uint32_t t0, uint32_t t1, float a[4], floa
         b[i] = __uint_as_float(r[4 + i]);
     }
 }
+__device__ __forceinline__ void ld16x128x2(uint32_t t0, uint32_t t1, float a[2], float b[2]) {
+    uint32_t r[4];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x128b.x1.b32 {%0,%1}, [%4];\n"
+        "tcgen05.ld.sync.aligned.16x128b.x1.b32 {%2,%3}, [%5];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+        : "r"(t0), "r"(t1)
+        : "memory");
+    a[0] = __uint_as_float(r[0]);
+    a[1] = __uint_as_float(r[1]);
+    b[0] = __uint_as_float(r[2]);
+    b[1] = __uint_as_float(r[3]);
+}
 
 // L2 prefetch of a contiguous range; skipped unless the address is 16-byte aligned (the size
 // is rounded down to a multiple of 16 bytes)
@@ -409,20 +437,6 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
     if (bytes && ((uintptr_t)p & 15u) == 0) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// 4 consecutive floats (16-byte aligned when NB % 4 == 0, else element by element)
-template <bool VEC>
-__device__ __forceinline__ void load4(const float* p, float v[4]) {
-    if constexpr (VEC) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(p));
-        v[0] = t.x;
-        v[1] = t.y;
-        v[2] = t.z;
-        v[3] = t.w;
-    } else {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = __ldg(p + i);
-    }
-}
 
 
 // named barrier of one context (256 threads, barrier id 1 + context)
@@ -532,8 +546,6 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     uint32_t phase = 0;
     const int wc = ct >> 5;                          // warp within the context
     const int qq = wc & 3, part = wc >> 2;           // TMEM lane quarter (warp % 4), column part (0, 1)
-    const bool has_row = lane < 16;                  // M = 64: rows in lanes 0-15 of each quarter
-    const int lrow = 16 * qq + lane;                 // this thread's accumulator row (if has_row)
     const uint32_t lane_base = (uint32_t)(qq * 32) << 16;
 
     const int64_t ntiles = (a.ne + ET - 1) / ET;
@@ -684,19 +696,17 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         }
         // ---- stage TMEM -> shared memory: point states (mean + deviation x factor) ----------------
         {
-            const bool own_ok = has_row && lrow < 5 * nel;
-            const int e = lrow / 5, v = lrow - 5 * (lrow / 5);
-            const float2 mr = own_ok ? sRow[lrow] : make_float2(0.f, 0.f);
-            float* dst = sU + e * USTR + v * VSTR;
+            // rows rA, rB of this thread (16x256b layout), columns 8 ch + cb, +1
+            const int rA = 16 * qq + (lane >> 2), rB = rA + 8, cb = 2 * (lane & 3);
+            const bool okA = rA < 5 * nel, okB = rB < 5 * nel;
+            const float2 mA = okA ? sRow[rA] : make_float2(0.f, 0.f), mB = okB ? sRow[rB] : make_float2(0.f, 0.f);
+            float* dA = sU + (rA / 5) * USTR + (rA % 5) * VSTR + cb;
+            float* dB = sU + (rB / 5) * USTR + (rB % 5) * VSTR + cb;
             for (int ch = part; ch * 8 < S::NPT; ch += 2) {
-                float val[8];
-                tc::ld8(tmem + lane_base + S::C_D1 + 8 * ch, val);
-                if (own_ok) {
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) val[t] = fmaf(val[t], mr.y, mr.x);
-                    *reinterpret_cast<float4*>(dst + 8 * ch) = make_float4(val[0], val[1], val[2], val[3]);
-                    *reinterpret_cast<float4*>(dst + 8 * ch + 4) = make_float4(val[4], val[5], val[6], val[7]);
-                }
+                float val[4];
+                ld16x256(tmem + lane_base + S::C_D1 + 8 * ch, val);
+                if (okA) *reinterpret_cast<float2*>(dA + 8 * ch) = make_float2(fmaf(val[0], mA.y, mA.x), fmaf(val[1], mA.y, mA.x));
+                if (okB) *reinterpret_cast<float2*>(dB + 8 * ch) = make_float2(fmaf(val[2], mB.y, mB.x), fmaf(val[3], mB.y, mB.x));
             }
         }
         tc::fence_before();
@@ -799,41 +809,40 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         }
         // the next tile's neighbour blocks (sC is free: this tile's traces are done)
         if (ct >= 128 && tile + tstride < ntiles) issue_neighbour_blocks<NV5>(a, tile + tstride, ct, sC);
-        // epilogue operands in flight while the tensor cores work: 4-mode chunks of this thread's row
-        constexpr int NCH = S::NCH;
-        constexpr bool VEC = NB % 4 == 0;
-        const bool row_ok = has_row && lrow < 5 * nel;
-        const int ee = lrow / 5, vv = lrow - 5 * (lrow / 5);
-        const int64_t gbase = (e0 + ee) * 5 * NB + vv * NB;
-        // chunks part, part + 2, part + 4 of this thread's row
-        const int nchunk = part < NCH ? (NCH - part + 1) / 2 : 0;
-        float uh[3][4], ul[3][4], u0h[3][4], u0l[3][4];
+        // epilogue operands in flight while the tensor cores work.  This thread holds rows rA, rB
+        // (16-lane layout) and, per column group g of its part, the mode pair (or single mode) below:
+        //   part 0: modes cb, cb+1 (columns 0..7);
+        //   part 1: modes 8 + cb, 9 + cb (columns 8..15) and 16 + lane % 4 (columns 16..19)
+        const int rA = 16 * qq + (lane >> 2), rB = rA + 8, cb = 2 * (lane & 3);
+        const bool okA = rA < 5 * nel, okB = rB < 5 * nel;
+        const int64_t gA = (e0 + rA / 5) * 5 * NB + (rA % 5) * NB, gB = (e0 + rB / 5) * 5 * NB + (rB % 5) * NB;
+        const int j0 = part == 0 ? cb : 8 + cb;                 // the mode pair
+        const bool pair_in = j0 < NB && N2 > 8 * part;
+        const int j1 = 16 + (lane & 3);                          // the single mode (part 1)
+        const bool one_in = part == 1 && N2 > 16 && j1 < NB;
+        // U_hi, U_lo, U0_hi, U0_lo at (row A | B) x (pair | single)
+        float u[2][4][3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
+        for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
-            for (int t = 0; t < 4; ++t) uh[k][t] = ul[k][t] = u0h[k][t] = u0l[k][t] = 0.f;
-        if (row_ok && a.mode != 0) {
+            for (int pl = 0; pl < 4; ++pl) u[rr][pl][0] = u[rr][pl][1] = u[rr][pl][2] = 0.f;
+        if (a.mode != 0) {
+            const float* pls[4] = {a.U_hi, a.U_lo, a.U0_hi, a.U0_lo};
+            const int npl = a.a != 0.f ? 4 : 2;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (k >= nchunk) break;
-                const int ch = part + 2 * k;
-                const int64_t o = gbase + 4 * ch;
-                if (VEC || 4 * ch + 4 <= NB) {
-                    load4<VEC>(a.U_hi + o, uh[k]);
-                    load4<VEC>(a.U_lo + o, ul[k]);
-                    if (a.a != 0.f) {
-                        load4<VEC>(a.U0_hi + o, u0h[k]);
-                        load4<VEC>(a.U0_lo + o, u0l[k]);
+            for (int rr = 0; rr < 2; ++rr) {
+                const bool ok = rr == 0 ? okA : okB;
+                const int64_t g = rr == 0 ? gA : gB;
+                if (!ok) continue;
+#pragma unroll
+                for (int pl = 0; pl < 4; ++pl) {
+                    if (pl >= npl) break;
+                    if (pair_in) {
+                        const float2 t2 = __ldg(reinterpret_cast<const float2*>(pls[pl] + g + j0));
+                        u[rr][pl][0] = t2.x;
+                        u[rr][pl][1] = t2.y;
                     }
-                } else {
-                    for (int t = 0; 4 * ch + t < NB; ++t) {
-                        uh[k][t] = __ldg(a.U_hi + o + t);
-                        ul[k][t] = __ldg(a.U_lo + o + t);
-                        if (a.a != 0.f) {
-                            u0h[k][t] = __ldg(a.U0_hi + o + t);
-                            u0l[k][t] = __ldg(a.U0_lo + o + t);
-                        }
-                    }
+                    if (one_in) u[rr][pl][2] = __ldg(pls[pl] + g + j1);
                 }
             }
         }
@@ -844,43 +853,55 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         tc::fence_after();
         // ---- epilogue: residual, or the RK stage in float-float -----------------------------------
         {
-            const float inv = row_ok ? sEl[ee * ELW + 49] : 0.f;
+            float d[2][3];   // R at (row A | B) x (pair 0, pair 1, single)
+            {
+                float x0[4], x1[4];
+                ld16x256x2(tmem + lane_base + S::C_D2 + 8 * part, tmem + lane_base + S::C_D2 + N2 + 8 * part, x0, x1);
+                d[0][0] = x0[0] + x1[0];
+                d[0][1] = x0[1] + x1[1];
+                d[1][0] = x0[2] + x1[2];
+                d[1][1] = x0[3] + x1[3];
+                d[0][2] = d[1][2] = 0.f;
+            }
+            if (part == 1 && N2 > 16) {
+                float y0[2], y1[2];
+                ld16x128x2(tmem + lane_base + S::C_D2 + 16, tmem + lane_base + S::C_D2 + N2 + 16, y0, y1);
+                d[0][2] = y0[0] + y1[0];
+                d[1][2] = y0[1] + y1[1];
+            }
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (k >= nchunk) break;
-                const int ch = part + 2 * k;
-                float d0[4], d1[4];
-                ld4x2(tmem + lane_base + S::C_D2 + 4 * ch, tmem + lane_base + S::C_D2 + N2 + 4 * ch, d0, d1);
-                if (!row_ok) continue;
-                float oh[4], ol[4];
+            for (int rr = 0; rr < 2; ++rr) {
+                const bool ok = rr == 0 ? okA : okB;
+                if (!ok) continue;
+                const int r = rr == 0 ? rA : rB;
+                const int64_t g = rr == 0 ? gA : gB;
+                const float inv = sEl[(r / 5) * ELW + 49];
+                float oh[3], ol[3];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const float R = (d0[t] + d1[t]) * inv;
+                for (int c = 0; c < 3; ++c) {
+                    const float R = d[rr][c] * inv;
                     if (a.mode == 0) {
-                        oh[t] = R;
-                        ol[t] = 0.f;
+                        oh[c] = R;
+                        ol[c] = 0.f;
                     } else {
                         // out = U + a (U0 - U) + b dt R: increment in FP32, float-float sum with U
-                        const float dlt = fmaf(a.a, (u0h[k][t] - uh[k][t]) + (u0l[k][t] - ul[k][t]), a.bdt * R);
-                        const float sm = uh[k][t] + dlt;
-                        const float bb = sm - uh[k][t];
-                        float err = (uh[k][t] - (sm - bb)) + (dlt - bb);
-                        err += ul[k][t];
-                        oh[t] = sm + err;
-                        ol[t] = err - (oh[t] - sm);
+                        const float uh = u[rr][0][c], ul = u[rr][1][c];
+                        const float dlt = fmaf(a.a, (u[rr][2][c] - uh) + (u[rr][3][c] - ul), a.bdt * R);
+                        const float sm = uh + dlt;
+                        const float bb = sm - uh;
+                        float err = (uh - (sm - bb)) + (dlt - bb);
+                        err += ul;
+                        oh[c] = sm + err;
+                        ol[c] = err - (oh[c] - sm);
                     }
                 }
-                const int64_t o = gbase + 4 * ch;
-                if (VEC) {
-                    *reinterpret_cast<float4*>(a.out_hi + o) = make_float4(oh[0], oh[1], oh[2], oh[3]);
-                    if (a.mode != 0) *reinterpret_cast<float4*>(a.out_lo + o) = make_float4(ol[0], ol[1], ol[2], ol[3]);
-                } else {
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        if (4 * ch + t >= NB) break;
-                        a.out_hi[o + t] = oh[t];
-                        if (a.mode != 0) a.out_lo[o + t] = ol[t];
-                    }
+                if (pair_in) {
+                    *reinterpret_cast<float2*>(a.out_hi + g + j0) = make_float2(oh[0], oh[1]);
+                    if (a.mode != 0) *reinterpret_cast<float2*>(a.out_lo + g + j0) = make_float2(ol[0], ol[1]);
+                }
+                if (one_in) {
+                    a.out_hi[g + j1] = oh[2];
+                    if (a.mode != 0) a.out_lo[g + j1] = ol[2];
                 }
             }
         }
