@@ -623,11 +623,24 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
             const float* ph = sPhiF + (fn * NQF + p) * NB;
             const float* cf = sC + c * NV5;
             float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            if constexpr (NB % 4 == 0) {
+                // rows of NB floats start on 16-byte boundaries: 4 modes per shared load
 #pragma unroll
-            for (int j = 0; j < NB; ++j) {
-                const float w = ph[j];
+                for (int j = 0; j < NB; j += 4) {
+                    const float4 w = *reinterpret_cast<const float4*>(ph + j);
 #pragma unroll
-                for (int v = 0; v < 5; ++v) acc[v] = fmaf(cf[v * NB + j], w, acc[v]);
+                    for (int v = 0; v < 5; ++v) {
+                        const float4 x = *reinterpret_cast<const float4*>(cf + v * NB + j);
+                        acc[v] = fmaf(x.x, w.x, fmaf(x.y, w.y, fmaf(x.z, w.z, fmaf(x.w, w.w, acc[v]))));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    const float w = ph[j];
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) acc[v] = fmaf(cf[v * NB + j], w, acc[v]);
+                }
             }
             float* nd = sN + c * 5 * NQF4 + p;
 #pragma unroll
