@@ -88,7 +88,7 @@ struct SPlan {
     static constexpr int NB = nb_of(P), NQ = nq_of(P), NQF = nqf_of(P), NF = 4 * NQF;
     static constexpr int NQ4 = (NQ + 3) / 4 * 4, NQF4 = (NQF + 3) / 4 * 4;
     // own-point table rows / D1 columns: face f point q at FPAD f + q, volume point q at 4 FPAD + q
-    static constexpr int FPAD = NQF <= 8 ? 8 : 16;
+    static constexpr int FPAD = NQF;
     static constexpr int NPT = 4 * FPAD + NQ;
     // operands hold interleaved split pairs: logical index k -> positions 2k (hi), 2k+1 (lo)
     static constexpr int K1 = r16(2 * NB);        // modes
@@ -959,9 +959,8 @@ int mixed_tab_halves(int p) {
 // f16 operand images of the basis tables in the canonical K-major layout, for
 // operands that hold interleaved (hi, lo) pairs at positions (2k, 2k+1):
 //   T1a / T1b [N1 points][K1]: (beta1 phi_hi, beta1 phi_hi) at mode j for point n
-//       (face f point q at row FPAD f + q, so that each face's rows start on an 8-row core
-//       matrix boundary; then the volume points); T1b: (beta1 phi_lo, 0); mode 0 is zero
-//       (the operands carry modes 1.. only)
+//       (face f point q at row FPAD f + q, then the volume points); T1b: (beta1 phi_lo, 0);
+//       mode 0 is zero (the operands carry modes 1.. only)
 //   T2a / T2b [N2 modes][K2]: logical k = (kk, q) -> beta2 w_q d_kk phi_j (q < Nq),
 //       then (f, q) -> beta2 wf_q phi_j on face f; (hi, hi) in T2a and (lo, 0) in T2b
 template <int P>
@@ -969,8 +968,7 @@ static void build_mixed_tables_t(const RefData& ref, std::vector<uint16_t>& out,
     using S = SPlan<P>;
     const TabLayout L(P);
     const double* t = ref.tab.data();
-    // own-point row n: face f point q at n = FPAD f + q (rows FPAD f + Nqf .. FPAD f + FPAD - 1
-    // zero), volume point q at n = 4 FPAD + q
+    // own-point row n: face f point q at n = FPAD f + q, volume point q at n = 4 FPAD + q
     auto phi_pt = [&](int n, int j) -> double {
         if (n < 4 * S::FPAD) {
             const int f = n / S::FPAD, q = n % S::FPAD;
