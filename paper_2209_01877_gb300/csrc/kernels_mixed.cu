@@ -102,10 +102,12 @@ struct SPlan {
     // tensor memory of a context: D1 (own points), D2[2] (projection, two K halves)
     static constexpr int C_D1 = 0, C_D2 = r16(N1);
     static_assert(C_D2 + 2 * N2 <= CTX_COLS, "tensor memory");
-    // point-state staging [ET][5][VSTR]: VSTR = 4 (mod 8) and >= the staged columns, so that the
-    // 16-byte stores of 8 consecutive rows (5e + v) and the volume-point loads avoid bank conflicts
+    // point-state staging [ET][5][VSTR]: VSTR = 8 (mod 32) and >= the staged columns, so USTR =
+    // 5 VSTR = 8 (mod 32) too; then row 5e + v starts at bank 8 (e + v) (mod 32), any 4
+    // consecutive rows start 8 banks apart (conflict-free 8-byte staging stores of a half warp),
+    // and the volume-point loads of 4 elements x 8 points hit 32 distinct banks
     static constexpr int SCOLS = (NPT + 7) / 8 * 8;
-    static constexpr int VSTR = SCOLS + ((4 - SCOLS % 8) + 8) % 8;
+    static constexpr int VSTR = SCOLS + ((8 - SCOLS % 32) + 32) % 32;
     static constexpr int USTR = 5 * VSTR;
     // per element: I[9], Is[9], Gbar_s[15], Fbar[15], ts, inv2, the A2 row parts of its 5 rows (int)
     static constexpr int ELW = 56;
