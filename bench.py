@@ -71,6 +71,11 @@ def replica_value(work_per_rank, t_local, world, device=None):
     return t, world * work_per_rank / t
 
 
+def flux_of(args):
+    """Numerical flux of the run: --flux, else the workload's."""
+    return getattr(args, "flux", None) or WORKLOADS[args.workload]["flux"]
+
+
 def order_of(args):
     """Element order of the run: --order, else the workload's (RCM where the workload names it,
     a Morton space-filling curve otherwise)."""
@@ -119,8 +124,8 @@ def algorithmic_model(p, ne, flux, s_state, stage):
 # bench scales it to the workload's tets; it reports null when the sources changed since.
 MEASURED_TRAFFIC = {
     # (precision, p, flux): (bytes per element per launch, source files, sha256[:16] of them)
-    ("mixed", 3, "roe"): (2051.8, ("kernels_mixed.cu", "tc_ops.cuh", "euler_device.cuh", "dg_internal.h"),
-                          "36d7ff6e74bf9114"),
+    ("mixed", 3, "roe"): (2039.7, ("kernels_mixed.cu", "tc_ops.cuh", "euler_device.cuh", "dg_internal.h"),
+                          "05051837af5e9355"),
     ("f64", 3, "roe"): (2071.0, ("kernels_simt.cu", "euler_device.cuh", "dg_internal.h"), "f4b7342c77ada5c7"),
 }
 
@@ -216,7 +221,7 @@ def run_ours(args, rank, world, device):
     from paper_2209_01877_gb300 import dg
 
     mesh, field, w = make_workload(args.workload)
-    p, flux = w["p"], w["flux"]
+    p, flux = w["p"], flux_of(args)
     precision = {"auto": dg.DG_MIXED_FP16, "mixed": dg.DG_MIXED_FP16, "fp64": dg.DG_FP64,
                  "fp32": dg.DG_FP32}[args.precision]
     fs = (0, 0, 0, 0, 0)
@@ -333,7 +338,7 @@ def run_ours(args, rank, world, device):
 
 
 # ---------------------------------------------------------------------------------------------
-def oracle_sample_rate(workload, nsample, reps=1, seed=11, warmup=0):
+def oracle_sample_rate(workload, nsample, reps=1, seed=11, warmup=0, flux=None):
     """The FP64 oracle's residual on a seeded sample of the workload's
     elements: (DOF-updates/s averaged over ``reps`` timed evaluations, seconds
     per evaluation, sample size, per-evaluation rates)."""
@@ -343,7 +348,7 @@ def oracle_sample_rate(workload, nsample, reps=1, seed=11, warmup=0):
     if w["box"]:
         from paper_2209_01877_gb300 import inputs as I
         fs = I.freestream_state(0.3)
-    P = Problem(mesh.tet_vid, mesh.tet_xyz, mesh.bc_tag if w["box"] else None, p=w["p"], flux=w["flux"],
+    P = Problem(mesh.tet_vid, mesh.tet_xyz, mesh.bc_tag if w["box"] else None, p=w["p"], flux=flux or w["flux"],
                 freestream=fs)
     rng = np.random.default_rng(seed)
     rows = np.sort(rng.choice(mesh.ne, size=min(nsample, mesh.ne), replace=False))
@@ -364,21 +369,21 @@ def oracle_sample_rate(workload, nsample, reps=1, seed=11, warmup=0):
     return float(np.mean(rates)), dt, len(rows), rates
 
 
-def _oracle_child(workload, nsample, reps, warmup=0):
+def _oracle_child(workload, nsample, reps, warmup=0, flux=None):
     """Run oracle_sample_rate in a child process pinned to one BLAS/OpenMP thread."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "r = bench.oracle_sample_rate(%r, %d, %d, warmup=%d); print(json.dumps(r))"
-            % (ROOT, workload, nsample, reps, warmup))
+            "r = bench.oracle_sample_rate(%r, %d, %d, warmup=%d, flux=%r); print(json.dumps(r))"
+            % (ROOT, workload, nsample, reps, warmup, flux))
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline_subprocess(workload, nsample, reps=1):
-    rate, sec, n, _ = _oracle_child(workload, nsample, reps)
+def cpu_baseline_subprocess(workload, nsample, reps=1, flux=None):
+    rate, sec, n, _ = _oracle_child(workload, nsample, reps, flux=flux)
     return {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
             "sample": f"FP64 oracle residual on {n} seeded elements of {workload} (with their neighbours' "
                       f"states), {reps} evaluation(s), {sec:.1f}s each, 1 thread"}
@@ -395,7 +400,7 @@ def run_reference(args):
         return
     cfg = config_of(args)
     n = max(200, SAMPLE.get(args.workload, 2000) // 3)
-    rate, sec, nrows, rates = _oracle_child(args.workload, n, args.steps, warmup=args.warmup)
+    rate, sec, nrows, rates = _oracle_child(args.workload, n, args.steps, warmup=args.warmup, flux=flux_of(args))
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "DOF-updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "dtype": "f64", "data": "synthetic", "config": cfg,
@@ -416,9 +421,9 @@ def config_of(args):
     desc = {"c1": "6^3x6 periodic cube", "c2": "48^3x6 periodic cube", "c3": "64^3x6 periodic cube",
             "c4": "32^3x6 periodic cube", "c5": "96x48x48x6 box channel", "c3s": "32^3x6 periodic cube"}
     oname = {"morton": "Morton order", "rcm": "RCM order", "asis": "input (random) order"}[order_of(args)]
-    return {"workload": f"{args.workload}: {desc[args.workload]}, P{w['p']}, {ne} tets, {w['flux']} flux, "
+    return {"workload": f"{args.workload}: {desc[args.workload]}, P{w['p']}, {ne} tets, {flux_of(args)} flux, "
                         f"jitter {w['jitter']}, {oname}, field {w['field']}",
-            "tets": ne, "order": w["p"], "flux": w["flux"], "dofs": ne * 5 * I.n_basis(w["p"]),
+            "tets": ne, "order": w["p"], "flux": flux_of(args), "dofs": ne * 5 * I.n_basis(w["p"]),
             "step": "one SSP-RK3 step = 3 fused residual+stage launches",
             "l2": "inputs larger than L2 (state >= 157 MB vs 129 MB L2)" if w["p"] >= 2 and ne > 100000
             else "state fits in L2 (small case)"}
@@ -441,7 +446,7 @@ def run_study(args):
     from paper_2209_01877_gb300.temporal import run_temporal_mp
     torch.cuda.set_device(0)
     mesh, field, w = make_workload(args.workload)
-    p, flux = w["p"], w["flux"]
+    p, flux = w["p"], flux_of(args)
     fl = dg.DG_ROE if flux == "roe" else dg.DG_RUSANOV
     tag = mesh.bc_tag if w["box"] else None
     fs = (0, 0, 0, 0, 0)
@@ -554,6 +559,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64", "fp32"])
+    ap.add_argument("--flux", default=None, choices=["roe", "rusanov"],
+                    help="numerical flux (default: the workload's; Roe for c3 and c5)")
     ap.add_argument("--order", default=None, choices=ORDER_NAMES,
                     help="element order (default: the workload's; RCM for c2, Morton otherwise)")
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 comparison leg of a mixed run")
@@ -584,7 +591,8 @@ def main():
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu_base = cpu_baseline_subprocess(args.workload, SAMPLE.get(args.workload, 20000), reps=2)
+            cpu_base = cpu_baseline_subprocess(args.workload, SAMPLE.get(args.workload, 20000), reps=2,
+                                               flux=flux_of(args))
         except Exception as e:  # reported, not fatal
             cpu_base = {"value": None, "error": str(e)[-300:]}
     r = run_ours(args, rank, world, device)
