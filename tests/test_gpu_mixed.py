@@ -148,3 +148,38 @@ def test_mixed_vortex_accuracy_within_2pct_of_fp64():
     print(f"vortex L2 density error: fp64 {e64:.4e} mixed {emx:.4e} rel diff {abs(emx - e64) / e64:.2e}, "
           f"rms coefficient difference {diff:.2e}")
     assert abs(emx - e64) <= 0.02 * e64
+
+
+# ---- full-size workloads in the benchmark's configuration (Morton order), sampled ------------
+def _sampled_mixed(m, flux, U_fn, freestream=None, nsample=1500, include=()):
+    from gpu_helpers import sample_elements
+    P = Problem(m.tet_vid, m.tet_xyz, m.bc_tag if not all(m.periodic) else None, p=3, flux=flux,
+                freestream=freestream)
+    U = U_fn(P)
+    R = gpu_residual(_mesh(m, 3, flux, fs=freestream, order="morton"), U)
+    rows = sample_elements(m.ne, nsample, include=include)
+    ref = P.residual(U, rows)
+    return max_rel_err(R[rows], ref, term_scale=residual_term_scale(P, U, rows))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("flux", ["roe", "rusanov"])
+def test_full_size_p3_64cube_mixed(flux):
+    """The 64^3 x 6 P3 vortex (1,572,864 tets) through the mixed stage kernel, sampled rows
+    against the oracle."""
+    m = I.make_periodic_cube(64, jitter=0.15)
+    assert _sampled_mixed(m, flux, lambda P: vortex_state(P, rule="volume")) < TOLMIX
+
+
+@pytest.mark.slow
+def test_full_size_p3_box_channel_mixed():
+    """The 96x48x48 x 6 P3 box channel (1,327,104 tets, slip walls and far field) through the
+    mixed stage kernel; boundary elements and the pulse region are always sampled."""
+    m = I.make_box_channel(96, 48, 48, jitter=0.15)
+    Uinf = I.freestream_state(0.3)
+    c = I.pulse_centre()
+    bnd = np.nonzero(np.any(m.bc_tag > 0, axis=1))[0][:300]
+    cent = m.tet_xyz.mean(axis=1)
+    pulse = np.nonzero(np.sum((cent - np.array(c)) ** 2, axis=1) < 0.1 ** 2)[0][:600]
+    U_fn = lambda P: P.project(lambda x: I.gaussian_pulse(x, c), rule="volume")
+    assert _sampled_mixed(m, "roe", U_fn, freestream=Uinf, include=np.concatenate([bnd, pulse])) < TOLMIX
