@@ -2,9 +2,9 @@
 // (tcgen05, sm_103a): one fused kernel per stage.
 //
 // Precision (per operation):
-//   * the dense contractions of Eq. 11's discretisation -- face traces and
-//     volume values of the element, traces of neighbours in other tiles, and
-//     the projection / lift back to the modes -- run as f16 x f16 -> f32 MMAs
+//   * the dense contractions of Eq. 11's discretisation -- the element's face
+//     traces and volume values, and the projection / lift back to the modes
+//     -- run as f16 x f16 -> f32 MMAs
 //     on split operands: x = x_hi + x_lo (two f16 numbers, power-of-two
 //     scaled per operand row), products hi*hi + hi*lo + lo*hi accumulated in
 //     f32 (effective operand precision ~2^-22).  The operands carry deviations
@@ -12,8 +12,8 @@
 //     in FP32) and F - F(mean state) for the projection (a constant flux
 //     integrates to zero against the basis gradients minus the face lift,
 //     both rules being exact to degree 2p);
-//   * Euler flux, Riemann solver, ghost states and J^-1 transforms in FP32 on
-//     the CUDA cores;
+//   * Euler flux, Riemann solver, ghost states, J^-1 transforms and the traces
+//     of neighbours in other tiles in FP32 on the CUDA cores;
 //   * the RK solution accumulation in float-float (the state is stored as two
 //     FP32 planes, ~48 significant bits); the stage increment a (U0 - U) +
 //     b dt R is formed in FP32 -- it is small against U, so its rounding sits
@@ -32,11 +32,13 @@
 // order are spatial neighbours); their traces are evaluated on the CUDA cores
 // in FP32 while the tensor cores work.  Per tile:
 //   build    operand rows of the own coefficients (modes 1..); the
-//            coefficient blocks of the neighbours in other tiles;
+//            neighbours' coefficient blocks were copied by cp.async while
+//            the previous tile's MMA 2 ran;
 //   MMA 1    own values at the 4 Nqf face points and the Nq volume points;
 //            meanwhile the neighbours' traces (FP32) and the per-element
 //            scaled J^-1 and mean-state fluxes;
-//   stage    TMEM -> shared memory (FP32 point states);
+//   stage    TMEM -> shared memory (FP32 point states; 16-lane TMEM loads so
+//            all 32 lanes of a warp work on the M = 64 accumulator);
 //   flux     volume points: contravariant flux deviation; face points:
 //            Rusanov / Roe flux (ghost state on boundary faces) written to
 //            the owner's and, for in-tile faces, the partner's operand;
