@@ -109,7 +109,12 @@ dg_status dg_project(const dg_mesh* mesh, const double* f, double* U, int on_dev
 
 /* Set / read the internal state (copied; caller order, FP64 [ne][5][Nb]).
  * on_device selects host or device memory for U.  With a host U,
- * dg_get_state synchronises the stream before it returns. */
+ * dg_get_state synchronises the stream before it returns.  A page-locked
+ * host U that is mapped into the device address space (cudaHostAlloc or
+ * cudaHostRegister memory) is read or written in place by the reordering
+ * kernel over the host link; any other host U goes through a device staging
+ * buffer.  With a page-locked host U, dg_set_state returns before U has been
+ * read: the caller keeps U unchanged until the stream has passed the call. */
 dg_status dg_set_state(dg_mesh* mesh, const double* U, int on_device, void* stream);
 dg_status dg_get_state(const dg_mesh* mesh, double* U, int on_device, void* stream);
 

@@ -28,6 +28,19 @@ dg_status cuda_fail(cudaError_t e, const char* where) {
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
+// The device address of a page-locked host buffer mapped into the device's address space
+// (cudaHostAlloc / cudaHostRegister memory under unified addressing), else NULL.  The
+// order-permuting gather and scatter kernels read and write such a buffer in place over the
+// host link, so no staging copy passes through device memory.
+void* mapped_host(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // bytes per stored coefficient: FP64, FP32, or a float-float pair (mixed precision)
 size_t real_size(int precision) { return precision == DG_FP32 ? sizeof(float) : 8; }
 bool is_mixed(const dg_mesh* m) { return m->precision == DG_MIXED_FP16; }
@@ -261,7 +274,10 @@ dg_status dg_set_state(dg_mesh* m, const double* U, int on_device, void* stream)
     if (!m || !U) return fail(DG_ERR_ARG, "mesh and U must be non-NULL");
     cudaStream_t s = as_stream(stream);
     const double* src = U;
-    if (!on_device) {
+    const void* mapped = on_device ? nullptr : mapped_host(U);
+    if (mapped) {
+        src = static_cast<const double*>(mapped);
+    } else if (!on_device) {
         if (!m->d_io) DG_CUDA(cudaMalloc(&m->d_io, (size_t)m->host.ne * 5 * m->nb * sizeof(double)));
         DG_CUDA(cudaMemcpyAsync(m->d_io, U, (size_t)m->host.ne * 5 * m->nb * sizeof(double), cudaMemcpyHostToDevice, s));
         src = m->d_io;
@@ -278,6 +294,11 @@ dg_status dg_get_state(const dg_mesh* mc, double* U, int on_device, void* stream
     cudaStream_t s = as_stream(stream);
     if (on_device) {
         DG_CUDA(dg::launch_scatter(m, m->d_B[0], U, s));
+        return DG_OK;
+    }
+    if (void* mapped = mapped_host(U)) {
+        DG_CUDA(dg::launch_scatter(m, m->d_B[0], static_cast<double*>(mapped), s));
+        DG_CUDA(cudaStreamSynchronize(s));
         return DG_OK;
     }
     if (!m->d_io) DG_CUDA(cudaMalloc(&m->d_io, (size_t)m->host.ne * 5 * m->nb * sizeof(double)));
