@@ -45,7 +45,7 @@ WORKLOADS = {
     # small case of the c3 kernel for profiler captures (state 157 MB > L2)
     "c3s": dict(n=32, p=3, jitter=0.15, flux="roe", field="vortex", box=False, order="morton"),
 }
-ORDER_NAMES = ("morton", "rcm", "asis")
+ORDER_NAMES = ("morton", "hilbert", "rcm", "asis")
 NB = {1: 4, 2: 10, 3: 20}
 NQ = {1: 4, 2: 14, 3: 24}
 NQF = {1: 3, 2: 6, 3: 12}
@@ -235,7 +235,8 @@ def run_ours(args, rank, world, device):
         from paper_2209_01877_gb300 import inputs as I
         fs = tuple(I.freestream_state(0.3))
     t0 = time.time()
-    ren = {"morton": dg.DG_ORDER_MORTON, "rcm": dg.DG_ORDER_RCM, "asis": dg.DG_ORDER_ASIS}[order_of(args)]
+    ren = {"morton": dg.DG_ORDER_MORTON, "hilbert": dg.DG_ORDER_HILBERT, "rcm": dg.DG_ORDER_RCM,
+           "asis": dg.DG_ORDER_ASIS}[order_of(args)]
     M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, None if not w["box"] else mesh.bc_tag, order=p, precision=precision,
                 flux=dg.DG_ROE if flux == "roe" else dg.DG_RUSANOV, renumber=ren, freestream=fs)
     U0 = M.project(field)
@@ -426,7 +427,8 @@ def config_of(args):
     ne = 6 * (w["n"] ** 3 if not w["box"] else int(np.prod(w["dims"])))
     desc = {"c1": "6^3x6 periodic cube", "c2": "48^3x6 periodic cube", "c3": "64^3x6 periodic cube",
             "c4": "32^3x6 periodic cube", "c5": "96x48x48x6 box channel", "c3s": "32^3x6 periodic cube"}
-    oname = {"morton": "Morton order", "rcm": "RCM order", "asis": "input (random) order"}[order_of(args)]
+    oname = {"morton": "Morton order", "hilbert": "Hilbert order", "rcm": "RCM order",
+             "asis": "input (random) order"}[order_of(args)]
     return {"workload": f"{args.workload}: {desc[args.workload]}, P{w['p']}, {ne} tets, {flux_of(args)} flux, "
                         f"jitter {w['jitter']}, {oname}, field {w['field']}",
             "tets": ne, "order": w["p"], "flux": flux_of(args), "dofs": ne * 5 * I.n_basis(w["p"]),
@@ -442,7 +444,7 @@ def run_study(args):
                  rest in FP64, k = 0, 20%, 50%, 80%, 100% of n; device time and
                  the RMS coefficient difference from the all-FP64 run.
     renumbering  (Sec. III-B, Tab. 1): element-adjacency bandwidth and RK-step
-                 throughput for the input (random) order, RCM and Morton.
+                 throughput for the input (random) order, RCM, Morton and Hilbert.
     adjoint      residual VJP and RK-step VJP throughput, and the checkpointed
                  multi-step adjoint (steps = --steps, checkpoints every 10).
     aux          the time-step reduction and the conservation / kinetic-energy
@@ -534,7 +536,7 @@ def run_study(args):
     else:
         rows = []
         for name, order in (("input (random)", dg.DG_ORDER_ASIS), ("RCM", dg.DG_ORDER_RCM),
-                            ("Morton", dg.DG_ORDER_MORTON)):
+                            ("Morton", dg.DG_ORDER_MORTON), ("Hilbert", dg.DG_ORDER_HILBERT)):
             prec = {"fp64": dg.DG_FP64, "fp32": dg.DG_FP32}.get(args.precision, dg.DG_MIXED_FP16)
             M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, tag, order=p, precision=prec, flux=fl, renumber=order,
                         freestream=fs)

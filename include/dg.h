@@ -53,7 +53,7 @@ typedef enum {
 
 enum { DG_FP64 = 0, DG_FP32 = 1, DG_MIXED_FP16 = 2, DG_MIXED_BF16 = 3 };
 enum { DG_RUSANOV = 0, DG_ROE = 1 };
-enum { DG_ORDER_ASIS = 0, DG_ORDER_RCM = 1, DG_ORDER_MORTON = 2 };
+enum { DG_ORDER_ASIS = 0, DG_ORDER_RCM = 1, DG_ORDER_MORTON = 2, DG_ORDER_HILBERT = 3 };
 enum { DG_BC_INTERIOR = 0, DG_BC_WALL = 1, DG_BC_FARFIELD = 2 };
 
 typedef struct dg_mesh dg_mesh;   /* opaque; owns every device buffer it allocates */
@@ -63,7 +63,7 @@ typedef struct {
     int precision;          /* DG_FP64 | DG_FP32 | DG_MIXED_FP16 | DG_MIXED_BF16 */
     int flux;               /* DG_RUSANOV | DG_ROE */
     double gamma;           /* ratio of specific heats, e.g. 1.4 */
-    int renumber;           /* DG_ORDER_ASIS | DG_ORDER_RCM | DG_ORDER_MORTON (Sec. III-B) */
+    int renumber;           /* DG_ORDER_ASIS | DG_ORDER_RCM | DG_ORDER_MORTON | DG_ORDER_HILBERT (Sec. III-B) */
     double roe_entropy_eps; /* Harten fix on the acoustic speeds, delta = eps * c_hat; 0 = off */
     double freestream[5];   /* conserved free-stream state for DG_BC_FARFIELD faces */
 } dg_config;
@@ -93,6 +93,22 @@ dg_status dg_mesh_destroy(dg_mesh* mesh);
  * element.  Any output pointer may be NULL. */
 dg_status dg_mesh_info(const dg_mesh* mesh, int64_t* n_faces, int64_t* n_bfaces,
                        int64_t* bandwidth_before, int64_t* bandwidth_after, int32_t* perm);
+
+/* The element order a mesh built from these arrays would use, computed on
+ * the host alone (no device is touched): the same validation and face
+ * matching as dg_mesh_create, then the renumbering.  Renumbering is the
+ * paper's grid-renumbering optimisation (Sec. III-B, Tab. 1): RCM on the
+ * element adjacency graph, or a space-filling curve of the element
+ * centroids (Morton or Hilbert) over their bounding box at 21 bits per axis.
+ *   tet_vid, tet_xyz, bc_tag, ne: as for dg_mesh_create (host, read only).
+ *   perm (host [ne], may be NULL): the internal position of every caller
+ *         element, as dg_mesh_info reports it.
+ *   bandwidth_before / bandwidth_after (may be NULL): max |i - j| over
+ *         adjacent elements before and after renumbering.
+ * Errors: DG_ERR_ARG (null arrays, ne out of range, bad renumber),
+ * DG_ERR_MESH. */
+dg_status dg_element_order(const int32_t* tet_vid, const double* tet_xyz, const int8_t* bc_tag, int64_t ne,
+                           int renumber, int32_t* perm, int64_t* bandwidth_before, int64_t* bandwidth_after);
 
 /* Sizes: Nb modes, Nq volume points, Nqf points per face. */
 dg_status dg_sizes(const dg_mesh* mesh, int* nb, int* nq, int* nqf);

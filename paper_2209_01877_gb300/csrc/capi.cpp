@@ -103,7 +103,7 @@ dg_status dg_mesh_create(const int32_t* tet_vid, const double* tet_xyz, const in
         return fail(DG_ERR_UNSUPPORTED, "the BF16 mixed form is not available in this build (use DG_MIXED_FP16)");
     if (cfg->flux != DG_RUSANOV && cfg->flux != DG_ROE) return fail(DG_ERR_ARG, "bad flux");
     if (!(cfg->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must exceed 1");
-    if (cfg->renumber < DG_ORDER_ASIS || cfg->renumber > DG_ORDER_MORTON) return fail(DG_ERR_ARG, "bad renumber");
+    if (cfg->renumber < DG_ORDER_ASIS || cfg->renumber > DG_ORDER_HILBERT) return fail(DG_ERR_ARG, "bad renumber");
     if (!(cfg->roe_entropy_eps >= 0.0)) return fail(DG_ERR_ARG, "roe_entropy_eps must be >= 0");
 
     dg_mesh* m = new dg_mesh();
@@ -217,6 +217,22 @@ dg_status dg_mesh_info(const dg_mesh* m, int64_t* n_faces, int64_t* n_bfaces, in
     if (bw_before) *bw_before = m->host.bw_before;
     if (bw_after) *bw_after = m->host.bw_after;
     if (perm) std::memcpy(perm, m->host.iperm.data(), m->host.iperm.size() * sizeof(int32_t));
+    return DG_OK;
+}
+
+dg_status dg_element_order(const int32_t* tet_vid, const double* tet_xyz, const int8_t* bc_tag, int64_t ne,
+                           int renumber, int32_t* perm, int64_t* bw_before, int64_t* bw_after) {
+    g_err.clear();
+    if (!tet_vid || !tet_xyz) return fail(DG_ERR_ARG, "tet_vid and tet_xyz must be non-NULL");
+    if (ne <= 0 || ne > (int64_t)INT32_MAX / 4) return fail(DG_ERR_ARG, "ne out of range");
+    if (renumber < DG_ORDER_ASIS || renumber > DG_ORDER_HILBERT) return fail(DG_ERR_ARG, "bad renumber");
+    dg::MeshHost h;
+    int code = DG_OK;
+    std::string err;
+    if (!dg::build_mesh(tet_vid, tet_xyz, bc_tag, ne, renumber, h, code, err)) return fail((dg_status)code, err);
+    if (perm) std::memcpy(perm, h.iperm.data(), h.iperm.size() * sizeof(int32_t));
+    if (bw_before) *bw_before = h.bw_before;
+    if (bw_after) *bw_after = h.bw_after;
     return DG_OK;
 }
 

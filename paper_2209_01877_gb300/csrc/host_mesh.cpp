@@ -8,8 +8,9 @@
 //     the own face's vertices gives the neighbour's);
 //   * element renumbering, the paper's grid-renumbering optimisation
 //     (Sec. III-B): reverse Cuthill-McKee on the element adjacency graph
-//     from a George-Liu pseudo-peripheral start node, or a Morton curve of
-//     the element centroids.  Ties are broken by the lower original index.
+//     from a George-Liu pseudo-peripheral start node, or a Morton or Hilbert
+//     curve of the element centroids.  Ties are broken by the lower original
+//     index.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -125,7 +126,37 @@ uint64_t spread3(uint64_t x) {
     return x;
 }
 
-void morton_order(const double* xyz, int64_t ne, std::vector<int32_t>& order) {
+// Position along the 3D Hilbert curve of a point on the 2^21 lattice, after J. Skilling,
+// "Programming the Hilbert curve" (AIP Conf. Proc. 707, 2004): the coordinates are turned in
+// place into the "transposed" index (from the top bit down, each lower-bit field is either
+// inverted in x or exchanged between x and the current axis; then a Gray decode), whose bits
+// are then interleaved, most significant level first, x before y before z.
+uint64_t hilbert_key(uint32_t x, uint32_t y, uint32_t z) {
+    uint32_t X[3] = {x, y, z};
+    for (uint32_t Q = 1u << 20; Q > 1; Q >>= 1) {
+        const uint32_t P = Q - 1;
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                const uint32_t t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    uint32_t t = 0;
+    for (uint32_t Q = 1u << 20; Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    for (uint32_t& v : X) v ^= t;
+    return (spread3(X[0]) << 2) | (spread3(X[1]) << 1) | spread3(X[2]);
+}
+
+// Space-filling-curve order of the element centroids, quantised to 21 bits per axis over their
+// bounding box: Morton (bit interleave, x lowest) or Hilbert.  Ties keep the input order.
+void curve_order(const double* xyz, int64_t ne, bool hilbert, std::vector<int32_t>& order) {
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     std::vector<double> c(3 * ne);
     for (int64_t e = 0; e < ne; ++e)
@@ -138,13 +169,13 @@ void morton_order(const double* xyz, int64_t ne, std::vector<int32_t>& order) {
         }
     std::vector<uint64_t> code(ne);
     for (int64_t e = 0; e < ne; ++e) {
-        uint64_t m = 0;
+        uint32_t q[3];
         for (int d = 0; d < 3; ++d) {
             double t = (c[3 * e + d] - lo[d]) / std::max(hi[d] - lo[d], 1e-300);
-            uint64_t q = (uint64_t)std::min(2097151.0, std::max(0.0, t * 2097151.0));
-            m |= spread3(q) << d;
+            q[d] = (uint32_t)std::min(2097151.0, std::max(0.0, t * 2097151.0));
         }
-        code[e] = m;
+        code[e] = hilbert ? hilbert_key(q[0], q[1], q[2])
+                          : spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
     }
     order.resize(ne);
     std::iota(order.begin(), order.end(), 0);
@@ -255,7 +286,8 @@ bool build_mesh(const int32_t* tet_vid, const double* tet_xyz, const int8_t* bc_
     // renumbering
     std::vector<int32_t> order;
     if (renumber == DG_ORDER_RCM) rcm_order(nbr_c, ne, order);
-    else if (renumber == DG_ORDER_MORTON) morton_order(tet_xyz, ne, order);
+    else if (renumber == DG_ORDER_MORTON || renumber == DG_ORDER_HILBERT)
+        curve_order(tet_xyz, ne, renumber == DG_ORDER_HILBERT, order);
     else { order.resize(ne); std::iota(order.begin(), order.end(), 0); }
     out.perm = order;
     out.iperm.assign(ne, -1);

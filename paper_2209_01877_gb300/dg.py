@@ -18,15 +18,15 @@ LIB_PATH = os.path.join(_HERE, "libdg.so")
 
 DG_FP64, DG_FP32, DG_MIXED_FP16, DG_MIXED_BF16 = 0, 1, 2, 3
 DG_RUSANOV, DG_ROE = 0, 1
-DG_ORDER_ASIS, DG_ORDER_RCM, DG_ORDER_MORTON = 0, 1, 2
+DG_ORDER_ASIS, DG_ORDER_RCM, DG_ORDER_MORTON, DG_ORDER_HILBERT = 0, 1, 2, 3
 DG_BC_INTERIOR, DG_BC_WALL, DG_BC_FARFIELD = 0, 1, 2
 STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_MESH", 3: "DG_ERR_CUDA", 4: "DG_ERR_OOM",
                 5: "DG_ERR_NONPHYSICAL", 6: "DG_ERR_NOSTATE", 7: "DG_ERR_UNSUPPORTED", 8: "DG_ERR_TIMEOUT"}
 
-EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_sizes", "dg_volume_points", "dg_project",
-            "dg_set_state", "dg_get_state", "dg_residual", "dg_rk_stage", "dg_rk3_step", "dg_stable_dt",
-            "dg_integrals", "dg_residual_vjp", "dg_rk3_step_vjp", "dg_kinetic_energy_grad", "dg_sync_status",
-            "dg_reference_data", "dg_conserved_totals_noalloc",
+EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_element_order", "dg_sizes",
+            "dg_volume_points", "dg_project", "dg_set_state", "dg_get_state", "dg_residual", "dg_rk_stage",
+            "dg_rk3_step", "dg_stable_dt", "dg_integrals", "dg_residual_vjp", "dg_rk3_step_vjp",
+            "dg_kinetic_energy_grad", "dg_sync_status", "dg_reference_data", "dg_conserved_totals_noalloc",
             "dg_last_error"]
 
 
@@ -58,6 +58,7 @@ def load():
             "dg_mesh_create": [vp, vp, vp, i64, C.POINTER(dg_config), vp, C.POINTER(vp)],
             "dg_mesh_destroy": [vp],
             "dg_mesh_info": [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), vp],
+            "dg_element_order": [vp, vp, vp, i64, C.c_int, vp, C.POINTER(i64), C.POINTER(i64)],
             "dg_sizes": [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
             "dg_volume_points": [vp, vp, C.c_int, vp],
             "dg_project": [vp, vp, vp, C.c_int, vp],
@@ -159,6 +160,25 @@ def dg_mesh_info(mesh, ne=None):
     _check(load().dg_mesh_info(mesh, C.byref(a), C.byref(b), C.byref(c), C.byref(d), pp))
     return {"n_faces": a.value, "n_bfaces": b.value, "bandwidth_before": c.value,
             "bandwidth_after": d.value, "perm": perm}
+
+
+def dg_element_order(tet_vid, tet_xyz, bc_tag=None, renumber=DG_ORDER_RCM):
+    """Host-only: (perm, bandwidth_before, bandwidth_after); perm[e] = internal position of e."""
+    vid, pv = _hptr(tet_vid, np.int32)
+    xyz, px = _hptr(tet_xyz, np.float64)
+    ne = vid.shape[0]
+    if vid.shape != (ne, 4) or xyz.shape != (ne, 4, 3):
+        raise ValueError("tet_vid must be [ne,4] and tet_xyz [ne,4,3]")
+    pb = None
+    if bc_tag is not None:
+        tag, pb = _hptr(bc_tag, np.int8)
+        if tag.shape != (ne, 4):
+            raise ValueError("bc_tag must be [ne,4]")
+    perm = np.empty(ne, dtype=np.int32)
+    b0, b1 = C.c_int64(), C.c_int64()
+    _check(load().dg_element_order(pv, px, pb, ne, int(renumber), C.c_void_p(perm.ctypes.data), C.byref(b0),
+                                   C.byref(b1)))
+    return perm, b0.value, b1.value
 
 
 def dg_sizes(mesh):

@@ -65,14 +65,15 @@ def test_mixed_residual_box(p, order):
     assert max_rel_err(Rg, R, term_scale=residual_term_scale(P, U)) < TOLMIX
 
 
-@pytest.mark.parametrize("order", ["morton", "rcm", "asis"])
+@pytest.mark.parametrize("order", ["morton", "hilbert", "rcm", "asis"])
 def test_mixed_residual_orders_agree(order):
     """Every element order gives the same residual up to FP32 round-off, whichever faces
     land inside a tile."""
     m = I.make_periodic_cube(5, jitter=0.15)
     P = Problem(m.tet_vid, m.tet_xyz, None, p=3, flux="roe")
     U = vortex_state(P, radius=0.2)
-    ren = {"morton": dg.DG_ORDER_MORTON, "rcm": dg.DG_ORDER_RCM, "asis": dg.DG_ORDER_ASIS}[order]
+    ren = {"morton": dg.DG_ORDER_MORTON, "hilbert": dg.DG_ORDER_HILBERT, "rcm": dg.DG_ORDER_RCM,
+           "asis": dg.DG_ORDER_ASIS}[order]
     M = dg.Mesh(m.tet_vid, m.tet_xyz, None, order=3, precision=dg.DG_MIXED_FP16, flux=dg.DG_ROE, renumber=ren)
     Rg = gpu_residual(M, U)
     assert max_rel_err(Rg, P.residual(U), term_scale=residual_term_scale(P, U)) < TOLMIX
