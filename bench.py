@@ -6,7 +6,7 @@ solver, lift, inverse mass, RK axpy).  Metric: residual DOF-updates per
 second = 3 * N_e * 5 * N_b / t_step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3]
-                    [--precision auto|fp64|fp32] [--impl ours|reference]
+                    [--precision auto|mixed|mixed-bf16|fp64|fp32] [--impl ours|reference]
 
 Workloads (seeded, synthetic; they stand in for the paper's 2D grids):
   c1  6^3 x 6 periodic cube, P1, jitter 10%   (1,296 tets)
@@ -124,9 +124,9 @@ def algorithmic_model(p, ne, flux, s_state, stage):
 # bench scales it to the workload's tets; it reports null when the sources changed since.
 MEASURED_TRAFFIC = {
     # (precision, p, flux): (bytes per element per launch, source files, sha256[:16] of them)
-    ("mixed", 3, "roe"): (2039.7, ("kernels_mixed.cu", "tc_ops.cuh", "euler_device.cuh", "dg_internal.h"),
-                          "da1edb273c93ca83"),
-    ("f64", 3, "roe"): (2071.0, ("kernels_simt.cu", "euler_device.cuh", "dg_internal.h"), "6b9668ac40d6bb50"),
+    ("mixed", 3, "roe"): (2039.5, ("kernels_mixed.cu", "tc_ops.cuh", "euler_device.cuh", "dg_internal.h"),
+                          "250e38dd31e72466"),
+    ("f64", 3, "roe"): (2072.8, ("kernels_simt.cu", "euler_device.cuh", "dg_internal.h"), "0a9c2f4b50d4b2ac"),
 }
 
 
@@ -228,8 +228,8 @@ def run_ours(args, rank, world, device):
 
     mesh, field, w = make_workload(args.workload)
     p, flux = w["p"], flux_of(args)
-    precision = {"auto": dg.DG_MIXED_FP16, "mixed": dg.DG_MIXED_FP16, "fp64": dg.DG_FP64,
-                 "fp32": dg.DG_FP32}[args.precision]
+    precision = {"auto": dg.DG_MIXED_FP16, "mixed": dg.DG_MIXED_FP16, "mixed-bf16": dg.DG_MIXED_BF16,
+                 "fp64": dg.DG_FP64, "fp32": dg.DG_FP32}[args.precision]
     fs = (0, 0, 0, 0, 0)
     if w["box"]:
         from paper_2209_01877_gb300 import inputs as I
@@ -311,7 +311,7 @@ def run_ours(args, rank, world, device):
                 "kernel": "k_residual<double,P,FLUX,RK>", "algorithmic_bytes_per_launch": bytes_per_launch,
                 "algorithmic_flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms}
     else:
-        kname = "k_residual<float,P,FLUX,RK>" if precision == dg.DG_FP32 else "k_stage_mixed<P,FLUX>"
+        kname = "k_residual<float,P,FLUX,RK>" if precision == dg.DG_FP32 else "k_stage_mixed<P,FLUX,BF16>"
         roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": hbm_achieved / peaks["hbm_gbs"], "traffic": None,
                 "peak_source": f"hbm_gbs of {peak_src} peaks", "kernel": kname,
@@ -337,7 +337,8 @@ def run_ours(args, rank, world, device):
         e2e = {"value": world * 3 * dofs * nrep / te, "unit": "DOF-updates/s", "h2d_bytes_per_step": dofs * 8,
                "d2h_bytes_per_step": dofs * 8, "steps": nrep}
     M.close()
-    pname = {dg.DG_FP64: "f64", dg.DG_FP32: "f32", dg.DG_MIXED_FP16: "f16x2-tc/f32/ff32"}[precision]
+    pname = {dg.DG_FP64: "f64", dg.DG_FP32: "f32", dg.DG_MIXED_FP16: "f16x2-tc/f32/ff32",
+             dg.DG_MIXED_BF16: "bf16x2-tc/f32/ff32"}[precision]
     roof["traffic"] = measured_traffic(pname, p, flux, ne)
     return dict(value=value, ms_per_step=ms_per_step, roofline=roof, clocks=clk, e2e=e2e, t_local=t_local,
                 precision=pname, ne=ne, p=p, flux=flux,
@@ -566,7 +567,7 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64", "fp32"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "mixed-bf16", "fp64", "fp32"])
     ap.add_argument("--flux", default=None, choices=["roe", "rusanov"],
                     help="numerical flux (default: the workload's; Roe for c3 and c5)")
     ap.add_argument("--order", default=None, choices=ORDER_NAMES,

@@ -14,7 +14,8 @@
  *   - the inverse mass matrix (diagonal: |det J| for the orthonormal basis);
  *   - explicit Runge-Kutta time marching (Sec. III; here SSP-RK3) and the
  *     global minimum of the local time step (Sec. III-C);
- *   - grid renumbering by reverse Cuthill-McKee (Sec. III-B).
+ *   - grid renumbering by reverse Cuthill-McKee (Sec. III-B), or by a Morton
+ *     or Hilbert curve of the element centroids.
  *
  * Conventions shared by every call:
  *   - Every call returns a dg_status; DG_OK is 0.  On failure
@@ -51,6 +52,13 @@ typedef enum {
     DG_ERR_TIMEOUT = 8       /* a bounded device wait gave up */
 } dg_status;
 
+/* Arithmetic of a mesh (the paper's mixed-precision study, Sec. III-B):
+ *   DG_FP64 / DG_FP32: the whole residual and RK update in that type (CUDA cores);
+ *   DG_MIXED_FP16: the contractions on the tensor cores on (hi, lo) f16 operand
+ *     pairs (~2^-22 relative), flux and Riemann solver in FP32, RK state in
+ *     float-float (two FP32 planes);
+ *   DG_MIXED_BF16: the same with bf16 pairs (~2^-16 relative per operand).
+ * The adjoint calls need DG_FP64 or DG_FP32. */
 enum { DG_FP64 = 0, DG_FP32 = 1, DG_MIXED_FP16 = 2, DG_MIXED_BF16 = 3 };
 enum { DG_RUSANOV = 0, DG_ROE = 1 };
 enum { DG_ORDER_ASIS = 0, DG_ORDER_RCM = 1, DG_ORDER_MORTON = 2, DG_ORDER_HILBERT = 3 };

@@ -43,7 +43,7 @@ void* mapped_host(const void* p) {
 
 // bytes per stored coefficient: FP64, FP32, or a float-float pair (mixed precision)
 size_t real_size(int precision) { return precision == DG_FP32 ? sizeof(float) : 8; }
-bool is_mixed(const dg_mesh* m) { return m->precision == DG_MIXED_FP16; }
+bool is_mixed(const dg_mesh* m) { return m->precision == DG_MIXED_FP16 || m->precision == DG_MIXED_BF16; }
 
 template <typename T>
 dg_status upload(T** dst, const T* src, size_t n, cudaStream_t s) {
@@ -99,8 +99,6 @@ dg_status dg_mesh_create(const int32_t* tet_vid, const double* tet_xyz, const in
     if (ne <= 0 || ne > (int64_t)INT32_MAX / 4) return fail(DG_ERR_ARG, "ne out of range");
     if (cfg->order < 1 || cfg->order > 3) return fail(DG_ERR_ARG, "order must be 1, 2 or 3");
     if (cfg->precision < DG_FP64 || cfg->precision > DG_MIXED_BF16) return fail(DG_ERR_ARG, "bad precision");
-    if (cfg->precision == DG_MIXED_BF16)
-        return fail(DG_ERR_UNSUPPORTED, "the BF16 mixed form is not available in this build (use DG_MIXED_FP16)");
     if (cfg->flux != DG_RUSANOV && cfg->flux != DG_ROE) return fail(DG_ERR_ARG, "bad flux");
     if (!(cfg->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must exceed 1");
     if (cfg->renumber < DG_ORDER_ASIS || cfg->renumber > DG_ORDER_HILBERT) return fail(DG_ERR_ARG, "bad renumber");
@@ -159,9 +157,9 @@ dg_status dg_mesh_create(const int32_t* tet_vid, const double* tet_xyz, const in
     DG_TRY(upload(&m->d_tab64, tab64.data(), tab64.size(), s));
     std::vector<float> tab32(m->ref.tab.begin(), m->ref.tab.end());
     std::vector<float> jinv32(m->host.jinv.begin(), m->host.jinv.end());
-    if (m->precision == DG_MIXED_FP16) {
+    if (is_mixed(m)) {
         std::vector<uint16_t> t16;
-        dg::build_mixed_tables(m->p, m->ref, t16, m->mix_inv_b1, m->mix_inv_b2);
+        dg::build_mixed_tables(m->p, m->precision == DG_MIXED_BF16, m->ref, t16, m->mix_inv_b1, m->mix_inv_b2);
         DG_TRY(upload(&m->d_tab16, t16.data(), t16.size(), s));
         std::vector<uint32_t> slot;
         std::vector<uint8_t> lists;

@@ -142,7 +142,8 @@ cudaError_t launch_ke_grad(dg_mesh* m, const double* U_user, double* out_user, c
 cudaError_t launch_residual_mixed(dg_mesh* m, const float* U_hi, const float* U_lo, const float* U0_hi,
                                   const float* U0_lo, float* out_hi, float* out_lo, int mode, double dt, double a,
                                   double b, cudaStream_t s);
-void build_mixed_tables(int p, const RefData& ref, std::vector<uint16_t>& out, float& inv_b1, float& inv_b2);
+void build_mixed_tables(int p, bool bf16, const RefData& ref, std::vector<uint16_t>& out, float& inv_b1,
+                        float& inv_b2);
 void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vector<uint8_t>& lists,
                        std::vector<int32_t>& hdr, std::vector<int32_t>& xnbr);
 dg_status set_error(dg_status code, const char* msg);   // sets dg_last_error() for the calling thread

@@ -7,7 +7,10 @@
 //     -- run as f16 x f16 -> f32 MMAs
 //     on split operands: x = x_hi + x_lo (two f16 numbers, power-of-two
 //     scaled per operand row), products hi*hi + hi*lo + lo*hi accumulated in
-//     f32 (effective operand precision ~2^-22).  The operands carry deviations
+//     f32 (effective operand precision ~2^-22).  The same kernel also runs on
+//     bf16 pairs (DG_MIXED_BF16: bf16 x bf16 -> f32 MMAs on the same split,
+//     ~2^-17 operand precision; the row scaling is then harmless but kept).
+//     The operands carry deviations
 //     only: modes >= 1 for the interpolations (the mode-0 mean is added back
 //     in FP32) and F - F(mean state) for the projection (a constant flux
 //     integrates to zero against the basis gradients minus the face lift,
@@ -50,6 +53,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "dg_internal.h"
@@ -172,11 +176,19 @@ __device__ __forceinline__ float pow2_scale(float x) {
     return (x > 0.f && eb >= 3 && eb < 255) ? __int_as_float((257 - eb) << 23) : 1.f;
 }
 
-// (hi, lo) f16 pair of x packed in one 32-bit word (hi in the low half = even K position)
+// (hi, lo) f16 pair (bf16 pair with BF) of x packed in one 32-bit word (hi in the low half = even
+// K position)
+template <bool BF>
 __device__ __forceinline__ uint32_t split_pair(float x) {
-    const float hi = __half2float(__float2half_rn(x));
-    const __half2 w = __floats2half2_rn(x, x - hi);
-    return *reinterpret_cast<const uint32_t*>(&w);
+    if constexpr (BF) {
+        const float hi = __bfloat162float(__float2bfloat16_rn(x));
+        const __nv_bfloat162 w = __floats2bfloat162_rn(x, x - hi);
+        return *reinterpret_cast<const uint32_t*>(&w);
+    } else {
+        const float hi = __half2float(__float2half_rn(x));
+        const __half2 w = __floats2half2_rn(x, x - hi);
+        return *reinterpret_cast<const uint32_t*>(&w);
+    }
 }
 
 // grad_x lambda_f (row f-1 of J^-1; lambda_0 = 1 - sum of the others)
@@ -343,7 +355,7 @@ __device__ __forceinline__ bool roe_f32(const float UL[5], const float UR[5], co
 // split-f16 operand row from Nb FP32 coefficients: modes 1.. scaled by a power of two that brings
 // their largest magnitude into [8, 16); returns (mean = sqrt6 c_0, inv_beta1 / scale), the factors
 // that turn the row's MMA result (against the beta1-scaled table) into point values
-template <int P>
+template <int P, bool BF>
 __device__ __forceinline__ float2 build_row(const float* __restrict__ c, __half* A, int r, float inv_beta1) {
     using S = SPlan<P>;
     constexpr int NB = S::NB, K1 = S::K1;
@@ -371,7 +383,7 @@ __device__ __forceinline__ float2 build_row(const float* __restrict__ c, __half*
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int j = ch * 4 + t;
-            w[t] = (j >= 1 && j < NB) ? split_pair(x[j] * sc) : 0u;
+            w[t] = (j >= 1 && j < NB) ? split_pair<BF>(x[j] * sc) : 0u;
         }
         *reinterpret_cast<uint4*>(A + tc::kmajor(r, 8 * ch, K1)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
@@ -488,7 +500,7 @@ __device__ __forceinline__ void issue_neighbour_blocks(const StageArgs& a, int64
     tc::cp_async_commit();
 }
 
-template <int P, int FLUX>
+template <int P, int FLUX, bool BF>
 __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     using S = SPlan<P>;
     constexpr int NB = S::NB, NQ = S::NQ, NQF = S::NQF, NQF4 = S::NQF4, FPAD = S::FPAD;
@@ -587,7 +599,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
             const int r = ct;
             if (r < 5 * nel) {
                 const int e = r / 5, v = r - 5 * e;
-                sRow[r] = build_row<P>(a.U_hi + ((e0 + e) * 5 + v) * NB, sA1, r, a.inv_beta1);
+                sRow[r] = build_row<P, BF>(a.U_hi + ((e0 + e) * 5 + v) * NB, sA1, r, a.inv_beta1);
             } else {
                 zero_row(sA1, r, K1);
             }
@@ -609,7 +621,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         if (ct == 0) {
             // descriptors advance by whole 16-byte units: a K step (256 B) adds 16
             constexpr uint64_t KSTEP = 16;
-            const uint32_t id1 = tc::idesc_f16(64, N1);
+            const uint32_t id1 = tc::idesc_f16(64, N1, BF);
             const uint64_t dA1 = tc::kdesc(sA1, 0, K1);
             const uint64_t dT1[2] = {tc::kdesc(sT1a, 0, K1), tc::kdesc(sT1b, 0, K1)};
 #pragma unroll
@@ -753,7 +765,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                     for (int k = 0; k < 3; ++k) {
                         uint32_t* A2k = reinterpret_cast<uint32_t*>(sA2 + kpart(k * NQ + q));
 #pragma unroll
-                        for (int v = 0; v < 5; ++v) A2k[rp[v] >> 1] = split_pair(G[k][v] - el[18 + 5 * k + v]);
+                        for (int v = 0; v < 5; ++v) A2k[rp[v] >> 1] = split_pair<BF>(G[k][v] - el[18 + 5 * k + v]);
                     }
                 } else {
                     const int j = i - NV;
@@ -791,7 +803,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                         uint32_t* A2k = reinterpret_cast<uint32_t*>(sA2 + kpart(__float_as_int(r2.z) + q));
 #pragma unroll
                         for (int v = 0; v < 5; ++v)
-                            A2k[__float_as_int(el[50 + v]) >> 1] = split_pair(fmaf(r0.w, H[v], -fb[v]));
+                            A2k[__float_as_int(el[50 + v]) >> 1] = split_pair<BF>(fmaf(r0.w, H[v], -fb[v]));
                     }
                     if (kind == SK_OWN) {
                         const float4 p0 = sRec[3 * sp], p1 = sRec[3 * sp + 1], p2 = sRec[3 * sp + 2];
@@ -800,7 +812,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                         uint32_t* A2k = reinterpret_cast<uint32_t*>(sA2 + kpart(__float_as_int(p2.z) + pq));
 #pragma unroll
                         for (int v = 0; v < 5; ++v)
-                            A2k[__float_as_int(elp[50 + v]) >> 1] = split_pair(-fmaf(p0.w, H[v], fbp[v]));
+                            A2k[__float_as_int(elp[50 + v]) >> 1] = split_pair<BF>(-fmaf(p0.w, H[v], fbp[v]));
                     }
                 }
             }
@@ -812,7 +824,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         // ---- MMA 2: projection onto the weighted basis gradients + face lift ----------------------
         if (ct == 0) {
             constexpr uint64_t KSTEP = 16;
-            const uint32_t id2 = tc::idesc_f16(64, N2);
+            const uint32_t id2 = tc::idesc_f16(64, N2, BF);
             const uint64_t dA2 = tc::kdesc(sA2, 0, K2), dTa = tc::kdesc(sT2a, 0, K2), dTb = tc::kdesc(sT2b, 0, K2);
             constexpr int KS = K2 / 16, KH = KS / 2;
 #pragma unroll
@@ -935,10 +947,10 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
 
 namespace {
 
-template <int P, int FLUX>
+template <int P, int FLUX, bool BF>
 cudaError_t slaunch(const StageArgs& sa, cudaStream_t s, int nsm) {
     using S = SPlan<P>;
-    auto k = k_stage_mixed<P, FLUX>;
+    auto k = k_stage_mixed<P, FLUX, BF>;
     static bool init = false;
     if (!init) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::BYTES);
@@ -960,7 +972,7 @@ int mixed_tab_halves(int p) {
     }
 }
 
-// f16 operand images of the basis tables in the canonical K-major layout, for
+// f16 (bf16 with bf16 set) operand images of the basis tables in the canonical K-major layout, for
 // operands that hold interleaved (hi, lo) pairs at positions (2k, 2k+1):
 //   T1a / T1b [N1 points][K1]: (beta1 phi_hi, beta1 phi_hi) at mode j for point n
 //       (face f point q at row FPAD f + q, then the volume points); T1b: (beta1 phi_lo, 0);
@@ -968,7 +980,8 @@ int mixed_tab_halves(int p) {
 //   T2a / T2b [N2 modes][K2]: logical k = (kk, q) -> beta2 w_q d_kk phi_j (q < Nq),
 //       then (f, q) -> beta2 wf_q phi_j on face f; (hi, hi) in T2a and (lo, 0) in T2b
 template <int P>
-static void build_mixed_tables_t(const RefData& ref, std::vector<uint16_t>& out, float& inv_b1, float& inv_b2) {
+static void build_mixed_tables_t(const RefData& ref, bool bf16, std::vector<uint16_t>& out, float& inv_b1,
+                                 float& inv_b2) {
     using S = SPlan<P>;
     const TabLayout L(P);
     const double* t = ref.tab.data();
@@ -1000,10 +1013,28 @@ static void build_mixed_tables_t(const RefData& ref, std::vector<uint16_t>& out,
     inv_b1 = (float)(1.0 / b1);
     inv_b2 = (float)(1.0 / b2);
     out.assign(S::TAB_HALVES, 0);
-    auto h16 = [](double x) { return __half_as_ushort(__double2half(x)); };
-    auto lo16 = [](double x) {
-        const double hi = (double)__half2float(__double2half(x));
-        return __half_as_ushort(__double2half(x - hi));
+    // the nearest operand-format value of x, as its bits and as a double
+    auto round16 = [bf16](double x, double& back) -> uint16_t {
+        uint16_t bits;
+        if (bf16) {
+            const __nv_bfloat16 b = __double2bfloat16(x);
+            back = (double)__bfloat162float(b);
+            std::memcpy(&bits, &b, sizeof bits);
+        } else {
+            const __half h = __double2half(x);
+            back = (double)__half2float(h);
+            bits = __half_as_ushort(h);
+        }
+        return bits;
+    };
+    auto h16 = [&](double x) {
+        double back;
+        return round16(x, back);
+    };
+    auto lo16 = [&](double x) {
+        double hi, back;
+        round16(x, hi);
+        return round16(x - hi, back);
     };
     auto images = [&](uint16_t* A, int rows, int K, int nrow_used, int nk, auto value) {
         uint16_t* Bimg = A + rows * K;
@@ -1020,10 +1051,11 @@ static void build_mixed_tables_t(const RefData& ref, std::vector<uint16_t>& out,
     images(out.data() + S::G_T2, S::N2, S::K2, S::NB, S::KL2, [&](int j, int kk) { return b2 * t2(j, kk); });
 }
 
-void build_mixed_tables(int p, const RefData& ref, std::vector<uint16_t>& out, float& inv_b1, float& inv_b2) {
-    if (p == 1) build_mixed_tables_t<1>(ref, out, inv_b1, inv_b2);
-    else if (p == 2) build_mixed_tables_t<2>(ref, out, inv_b1, inv_b2);
-    else build_mixed_tables_t<3>(ref, out, inv_b1, inv_b2);
+void build_mixed_tables(int p, bool bf16, const RefData& ref, std::vector<uint16_t>& out, float& inv_b1,
+                        float& inv_b2) {
+    if (p == 1) build_mixed_tables_t<1>(ref, bf16, out, inv_b1, inv_b2);
+    else if (p == 2) build_mixed_tables_t<2>(ref, bf16, out, inv_b1, inv_b2);
+    else build_mixed_tables_t<3>(ref, bf16, out, inv_b1, inv_b2);
 }
 
 // Tile metadata of the fused kernel (host, once per mesh): for every tile of ET consecutive
@@ -1110,10 +1142,17 @@ cudaError_t launch_residual_mixed(dg_mesh* m, const float* U_hi, const float* U_
     cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
     if (e != cudaSuccess) return e;
     const bool roe = m->flux == DG_ROE;
+    if (m->precision == DG_MIXED_BF16) {
+        switch (m->p) {
+            case 1: return roe ? slaunch<1, DG_ROE, true>(r, s, nsm) : slaunch<1, DG_RUSANOV, true>(r, s, nsm);
+            case 2: return roe ? slaunch<2, DG_ROE, true>(r, s, nsm) : slaunch<2, DG_RUSANOV, true>(r, s, nsm);
+            default: return roe ? slaunch<3, DG_ROE, true>(r, s, nsm) : slaunch<3, DG_RUSANOV, true>(r, s, nsm);
+        }
+    }
     switch (m->p) {
-        case 1: return roe ? slaunch<1, DG_ROE>(r, s, nsm) : slaunch<1, DG_RUSANOV>(r, s, nsm);
-        case 2: return roe ? slaunch<2, DG_ROE>(r, s, nsm) : slaunch<2, DG_RUSANOV>(r, s, nsm);
-        default: return roe ? slaunch<3, DG_ROE>(r, s, nsm) : slaunch<3, DG_RUSANOV>(r, s, nsm);
+        case 1: return roe ? slaunch<1, DG_ROE, false>(r, s, nsm) : slaunch<1, DG_RUSANOV, false>(r, s, nsm);
+        case 2: return roe ? slaunch<2, DG_ROE, false>(r, s, nsm) : slaunch<2, DG_RUSANOV, false>(r, s, nsm);
+        default: return roe ? slaunch<3, DG_ROE, false>(r, s, nsm) : slaunch<3, DG_RUSANOV, false>(r, s, nsm);
     }
 }
 

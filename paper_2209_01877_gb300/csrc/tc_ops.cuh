@@ -29,9 +29,11 @@ __device__ __forceinline__ uint64_t kdesc(const void* base, int ks, int K) {
     return desc(smem_u32(base) + ks * 256, 128, (K >> 3) * 128);
 }
 
-// instruction descriptor: f16 x f16 -> f32, both operands K-major, M x N
-__host__ __device__ constexpr uint32_t idesc_f16(int m, int n) {
-    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+// instruction descriptor of kind::f16: f16 x f16 -> f32, or bf16 x bf16 -> f32 with bf16 set (A and
+// B always take the same format), both operands K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n, bool bf16 = false) {
+    return (1u << 4) | (bf16 ? (1u << 7) | (1u << 10) : 0u) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {

@@ -6,7 +6,7 @@ from paper_2209_01877_gb300 import dg
 from paper_2209_01877_gb300 import inputs as I
 
 FLUX = {"rusanov": dg.DG_RUSANOV, "roe": dg.DG_ROE}
-PREC = {"fp64": dg.DG_FP64, "fp32": dg.DG_FP32, "mixed": dg.DG_MIXED_FP16}
+PREC = {"fp64": dg.DG_FP64, "fp32": dg.DG_FP32, "mixed": dg.DG_MIXED_FP16, "mixed-bf16": dg.DG_MIXED_BF16}
 
 
 def torch_cuda():

@@ -26,6 +26,9 @@ from gpu_helpers import gpu_residual, max_rel_err, residual_term_scale, torch_cu
 
 pytestmark = pytest.mark.gpu
 TOLMIX = 5e-6
+# bf16 pairs (DG_MIXED_BF16): 8 significant bits each, ~2^-16 = 1.5e-5 relative per operand, so
+# the product error is 3 x 1.5e-5 and the chain above gives ~6e-5; factor 5 margin
+TOLBF = 3e-4
 
 
 # element orders: a space-filling curve puts most faces inside one 24-element tile (evaluated
@@ -77,6 +80,43 @@ def test_mixed_residual_orders_agree(order):
     M = dg.Mesh(m.tet_vid, m.tet_xyz, None, order=3, precision=dg.DG_MIXED_FP16, flux=dg.DG_ROE, renumber=ren)
     Rg = gpu_residual(M, U)
     assert max_rel_err(Rg, P.residual(U), term_scale=residual_term_scale(P, U)) < TOLMIX
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("flux", ["rusanov", "roe"])
+def test_mixed_bf16_residual_periodic(p, flux):
+    """The same tensor-core kernel on bf16 operand pairs."""
+    m = I.make_periodic_cube(4, jitter=0.15)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=p, flux=flux)
+    U = vortex_state(P, radius=0.15)
+    R = P.residual(U)
+    Rg = gpu_residual(_mesh(m, p, flux, precision=dg.DG_MIXED_BF16), U)
+    err = max_rel_err(Rg, R, term_scale=residual_term_scale(P, U))
+    assert err < TOLBF
+    # bf16 pairs carry fewer bits than f16 pairs: the f16 form is the closer one
+    assert max_rel_err(gpu_residual(_mesh(m, p, flux), U), R, term_scale=residual_term_scale(P, U)) < err
+
+
+def test_mixed_bf16_box_and_rk_steps():
+    m = I.make_box_channel(4, 3, 3, lengths=(2.0, 1.0, 1.0), jitter=0.15)
+    fs = I.freestream_state(0.3)
+    P = Problem(m.tet_vid, m.tet_xyz, m.bc_tag, p=3, flux="roe", freestream=fs)
+    U = P.project(lambda x: I.gaussian_pulse(x, (0.9, 0.5, 0.5), width=0.3))
+    Rg = gpu_residual(_mesh(m, 3, "roe", precision=dg.DG_MIXED_BF16, fs=fs), U)
+    assert max_rel_err(Rg, P.residual(U), term_scale=residual_term_scale(P, U)) < TOLBF
+    # 10 RK steps: the f16 form's bar (1e-6 of the state) scaled by the operand precision ratio 2^6
+    m = I.make_periodic_cube(4, jitter=0.15)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=3, flux="roe")
+    U0 = vortex_state(P, radius=0.15)
+    dt = P.stable_dt(U0, 0.1)
+    ref = P.rk3(U0, dt, 10)
+    M = _mesh(m, 3, "roe", precision=dg.DG_MIXED_BF16)
+    dg.dg_set_state(M.handle, U0)
+    dg.dg_rk3_step(M.handle, dt, 10)
+    U1 = np.empty_like(U0)
+    dg.dg_get_state(M.handle, U1)
+    dg.dg_sync_status(M.handle)
+    assert np.abs(U1 - ref).max() < 64e-6 * np.abs(ref).max()
 
 
 def test_mixed_ragged_tile_and_free_stream():

@@ -136,7 +136,7 @@ def test_config1_one_rk3_step():
     assert max_rel_err(U1, ref) < 1e-14
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed", "mixed-bf16"])
 def test_state_pinned_host_matches_pageable(precision):
     """A page-locked host buffer is read and written in place by the reordering kernels; the
     state it sets and the values it returns are bit-identical to the staged (pageable) path."""
