@@ -449,7 +449,11 @@ def run_study(args):
     adjoint      residual VJP and RK-step VJP throughput, and the checkpointed
                  multi-step adjoint (steps = --steps, checkpoints every 10).
     aux          the time-step reduction and the conservation / kinetic-energy
-                 sums (device time per call)."""
+                 sums (device time per call).
+    conservation (periodic workloads) change of the conserved totals over
+                 --steps SSP-RK3 steps (FP64 capped at 50) for FP64 and both
+                 mixed forms: with no boundary flux it is the discrete
+                 conservation drift itself."""
     import torch
     from paper_2209_01877_gb300 import dg
     from paper_2209_01877_gb300.temporal import run_temporal_mp
@@ -534,6 +538,30 @@ def run_study(args):
         t_int = (time.perf_counter() - t0) / n
         out.update({"stable_dt_ms_incl_sync": t_dt * 1e3, "integrals_ms_incl_sync": t_int * 1e3,
                     "tets": mesh.ne})
+    elif args.study == "conservation":
+        if w["box"]:
+            raise SystemExit("the conservation study needs a periodic workload (no boundary flux)")
+        ren = {"morton": dg.DG_ORDER_MORTON, "hilbert": dg.DG_ORDER_HILBERT, "rcm": dg.DG_ORDER_RCM,
+               "asis": dg.DG_ORDER_ASIS}[order_of(args)]
+        rows = []
+        for pname, prec in (("f64", dg.DG_FP64), ("f16x2-tc/f32/ff32", dg.DG_MIXED_FP16),
+                            ("bf16x2-tc/f32/ff32", dg.DG_MIXED_BF16)):
+            nsteps = min(args.steps, 50) if prec == dg.DG_FP64 else args.steps
+            M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, None, order=p, precision=prec, flux=fl, renumber=ren)
+            dg.dg_set_state(M.handle, M.project(field))
+            t0, _ = dg.dg_integrals(M.handle)
+            dt = dg.dg_stable_dt(M.handle, 0.1)
+            dg.dg_rk3_step(M.handle, dt, nsteps)
+            t1, _ = dg.dg_integrals(M.handle)
+            dg.dg_sync_status(M.handle)
+            M.close()
+            d = t1 - t0
+            rows.append({"precision": pname, "steps": nsteps, "dt": dt, "totals_start": t0.tolist(),
+                         "drift": d.tolist(),
+                         "rel_drift_mass": abs(d[0]) / abs(t0[0]),
+                         "rel_drift_momentum": float(np.linalg.norm(d[1:4]) / np.linalg.norm(t0[1:4])),
+                         "rel_drift_energy": abs(d[4]) / abs(t0[4])})
+        out.update({"rows": rows, "note": "periodic domain: the change of the totals is the drift itself"})
     else:
         rows = []
         for name, order in (("input (random)", dg.DG_ORDER_ASIS), ("RCM", dg.DG_ORDER_RCM),
@@ -573,7 +601,7 @@ def main():
     ap.add_argument("--order", default=None, choices=ORDER_NAMES,
                     help="element order (default: the workload's; RCM for c2, Morton otherwise)")
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 comparison leg of a mixed run")
-    ap.add_argument("--study", choices=["temporal-mp", "renumbering", "adjoint", "aux"], default=None,
+    ap.add_argument("--study", choices=["temporal-mp", "renumbering", "adjoint", "aux", "conservation"], default=None,
                     help="print a study table instead of the benchmark line")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
