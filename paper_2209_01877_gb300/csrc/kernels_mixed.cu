@@ -105,7 +105,7 @@ struct SPlan {
     static constexpr int N2 = r8(NB);
     // f16 table images in global memory (halves): T1 a|b, T2 a|b
     static constexpr int G_T1 = 0, G_T2 = 2 * N1 * K1, TAB_HALVES = G_T2 + 2 * N2 * K2;
-    // tensor memory of a context: D1 (own points), D2[2] (projection, two K halves)
+    // tensor memory of a context: D1 (own points), D2 (projection: hi-table and lo-table products)
     static constexpr int C_D1 = 0, C_D2 = r16(N1);
     static_assert(C_D2 + 2 * N2 <= CTX_COLS, "tensor memory");
     // point-state staging [ET][5][VSTR]: VSTR = 8 (mod 32) and >= the staged columns, so USTR =
@@ -513,7 +513,6 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     const __half* sT1a = reinterpret_cast<const __half*>(smem + S::O_T1);
     const __half* sT1b = sT1a + N1 * K1;
     const __half* sT2a = reinterpret_cast<const __half*>(smem + S::O_T2);
-    const __half* sT2b = sT2a + N2 * K2;
     unsigned char* cx = smem + S::O_CTX + ctx * S::CTX_BYTES;
     __half* sA1 = reinterpret_cast<__half*>(cx + S::X_AU);
     float* sC = reinterpret_cast<float*>(cx + S::X_C);   // neighbour coefficient blocks (next tile's in flight)
@@ -822,18 +821,16 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         ctx_sync(bar_id);
         tc::fence_after();
         // ---- MMA 2: projection onto the weighted basis gradients + face lift ----------------------
+        // T2b follows T2a in shared memory in the same K-major layout, so [T2a; T2b] is one operand
+        // of 2 N2 rows: one MMA per K step writes the hi-table products to columns [0, N2) and the
+        // lo-table products to [N2, 2 N2); the epilogue adds the two
         if (ct == 0) {
             constexpr uint64_t KSTEP = 16;
-            const uint32_t id2 = tc::idesc_f16(64, N2, BF);
-            const uint64_t dA2 = tc::kdesc(sA2, 0, K2), dTa = tc::kdesc(sT2a, 0, K2), dTb = tc::kdesc(sT2b, 0, K2);
-            constexpr int KS = K2 / 16, KH = KS / 2;
+            const uint32_t id2 = tc::idesc_f16(64, 2 * N2, BF);
+            const uint64_t dA2 = tc::kdesc(sA2, 0, K2), dT2 = tc::kdesc(sT2a, 0, K2);
 #pragma unroll
-            for (int ks = 0; ks < KS; ++ks) {
-                const uint32_t dcol = tmem + S::C_D2 + (ks < KH ? 0 : N2);
-                const uint32_t first = (ks == 0 || ks == KH) ? 0u : 1u;
-                tc::mma(dcol, dA2 + KSTEP * ks, dTa + KSTEP * ks, id2, first);
-                tc::mma(dcol, dA2 + KSTEP * ks, dTb + KSTEP * ks, id2, 1u);
-            }
+            for (int ks = 0; ks < K2 / 16; ++ks)
+                tc::mma(tmem + S::C_D2, dA2 + KSTEP * ks, dT2 + KSTEP * ks, id2, ks != 0);
             tc::commit(mbar);
         }
         // the next tile's neighbour blocks (sC is free: this tile's traces are done)
