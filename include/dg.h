@@ -48,7 +48,7 @@ typedef enum {
     DG_ERR_OOM = 4,          /* device allocation failed */
     DG_ERR_NONPHYSICAL = 5,  /* the device saw rho <= 0, p <= 0 or a non-finite value */
     DG_ERR_NOSTATE = 6,      /* the call needs a state set by dg_set_state */
-    DG_ERR_UNSUPPORTED = 7,  /* valid request this build does not implement */
+    DG_ERR_UNSUPPORTED = 7,  /* valid request the library does not implement */
     DG_ERR_TIMEOUT = 8       /* a bounded device wait gave up */
 } dg_status;
 
