@@ -450,6 +450,8 @@ def run_study(args):
                  multi-step adjoint (steps = --steps, checkpoints every 10).
     aux          the time-step reduction and the conservation / kinetic-energy
                  sums (device time per call).
+    launch       device time per RK3 step of dg_rk3_step (a replayed CUDA graph on
+                 small meshes) against one dg_rk_stage launch per stage.
     conservation (periodic workloads) change of the conserved totals over
                  --steps SSP-RK3 steps (FP64 capped at 50) for FP64 and both
                  mixed forms: with no boundary flux it is the discrete
@@ -538,6 +540,34 @@ def run_study(args):
         t_int = (time.perf_counter() - t0) / n
         out.update({"stable_dt_ms_incl_sync": t_dt * 1e3, "integrals_ms_incl_sync": t_int * 1e3,
                     "tets": mesh.ne})
+    elif args.study == "launch":
+        prec = {"fp64": dg.DG_FP64, "fp32": dg.DG_FP32, "mixed-bf16": dg.DG_MIXED_BF16}.get(args.precision,
+                                                                                         dg.DG_MIXED_FP16)
+        M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, tag, order=p, precision=prec, flux=fl, freestream=fs)
+        dg.dg_set_state(M.handle, M.project(field))
+        dt = dg.dg_stable_dt(M.handle, 0.1)
+        n = max(args.steps, 8)
+        dg.dg_rk3_step(M.handle, dt, 8)
+        for st in (1, 2, 3):
+            dg.dg_rk_stage(M.handle, st, dt)
+        torch.cuda.synchronize()
+        res = {}
+        for name in ("dg_rk3_step", "dg_rk_stage x 3"):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            if name == "dg_rk3_step":
+                dg.dg_rk3_step(M.handle, dt, n)
+            else:
+                for _ in range(n):
+                    for st in (1, 2, 3):
+                        dg.dg_rk_stage(M.handle, st, dt)
+            b.record()
+            torch.cuda.synchronize()
+            res[name] = a.elapsed_time(b) * 1e3 / n
+        dg.dg_sync_status(M.handle)
+        M.close()
+        out.update({"steps": n, "tets": mesh.ne, "us_per_step": res,
+                    "note": "dg_rk3_step replays a CUDA graph of 8 captured steps on meshes of <= 65536 tets"})
     elif args.study == "conservation":
         if w["box"]:
             raise SystemExit("the conservation study needs a periodic workload (no boundary flux)")
@@ -601,7 +631,8 @@ def main():
     ap.add_argument("--order", default=None, choices=ORDER_NAMES,
                     help="element order (default: the workload's; RCM for c2, Morton otherwise)")
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 comparison leg of a mixed run")
-    ap.add_argument("--study", choices=["temporal-mp", "renumbering", "adjoint", "aux", "conservation"], default=None,
+    ap.add_argument("--study", choices=["temporal-mp", "renumbering", "adjoint", "aux", "conservation", "launch"],
+                    default=None,
                     help="print a study table instead of the benchmark line")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

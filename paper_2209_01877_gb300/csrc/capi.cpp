@@ -70,6 +70,8 @@ void free_mesh(dg_mesh* m) {
     for (auto& b : m->d_B) cudaFree(b);
     for (auto& b : m->d_V) cudaFree(b);
     cudaFree(m->d_io);
+    if (m->rk_exec) cudaGraphExecDestroy(m->rk_exec);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     cudaFree(m->d_red);
     cudaFree(m->d_status);
     if (m->h_red) cudaFreeHost(m->h_red);
@@ -354,31 +356,74 @@ cudaError_t stage_launch(dg_mesh* m, void* U, void* U0, void* out, double dt, do
     float* o = static_cast<float*>(out);
     return dg::launch_residual_mixed(m, u, u + n, u0, u0 ? u0 + n : nullptr, o, o + n, 1, dt, a, b, s);
 }
+
+// SSP-RK3 stage `stage` (1..3) on the state buffers: U1 = U + dt R(U); U2 = 3/4 U + 1/4 (U1 + dt R(U1));
+// U <- 1/3 U + 2/3 (U2 + dt R(U2))
+cudaError_t rk_stage_launch(dg_mesh* m, int stage, double dt, cudaStream_t s) {
+    void** B = m->d_B;
+    if (stage == 1) return stage_launch(m, B[0], nullptr, B[1], dt, 0.0, 1.0, s);
+    if (stage == 2) return stage_launch(m, B[1], B[0], B[2], dt, 0.75, 0.25, s);
+    return stage_launch(m, B[2], B[0], B[0], dt, 1.0 / 3.0, 2.0 / 3.0, s);
+}
+
+// A mesh this small is bound by launch latency: dg_rk3_step replays a CUDA graph of GRAPH_STEPS
+// captured steps (3 stage launches each) instead of launching every stage from the host.
+constexpr int64_t GRAPH_MAX_NE = 65536;
+constexpr int GRAPH_STEPS = 8;
+
+// the mesh's graph of GRAPH_STEPS steps at this dt, captured on its private stream when missing
+// or captured at another dt (the buffers and tables it launches on are fixed per mesh)
+cudaError_t rk_graph(dg_mesh* m, double dt) {
+    if (m->rk_exec && m->rk_graph_dt == dt) return cudaSuccess;
+    if (m->rk_exec) {
+        cudaGraphExecDestroy(m->rk_exec);
+        m->rk_exec = nullptr;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!m->cap_stream) e = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t el = cudaSuccess;
+    for (int n = 0; n < GRAPH_STEPS && el == cudaSuccess; ++n)
+        for (int st = 1; st <= 3 && el == cudaSuccess; ++st) el = rk_stage_launch(m, st, dt, m->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(m->cap_stream, &g);
+    if (el != cudaSuccess) e = el;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&m->rk_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        m->rk_exec = nullptr;
+        return e;
+    }
+    m->rk_graph_dt = dt;
+    return cudaSuccess;
+}
 }  // namespace
 
 dg_status dg_rk_stage(dg_mesh* m, int stage, double dt, void* stream) {
     if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
     if (!m->has_state) return fail(DG_ERR_NOSTATE, "no state set");
     if (!(dt >= 0.0)) return fail(DG_ERR_ARG, "dt must be >= 0");
-    cudaStream_t s = as_stream(stream);
-    void** B = m->d_B;
-    switch (stage) {
-        case 1: DG_CUDA(stage_launch(m, B[0], nullptr, B[1], dt, 0.0, 1.0, s)); break;
-        case 2: DG_CUDA(stage_launch(m, B[1], B[0], B[2], dt, 0.75, 0.25, s)); break;
-        case 3: DG_CUDA(stage_launch(m, B[2], B[0], B[0], dt, 1.0 / 3.0, 2.0 / 3.0, s)); break;
-        default: return fail(DG_ERR_ARG, "stage must be 1, 2 or 3");
-    }
+    if (stage < 1 || stage > 3) return fail(DG_ERR_ARG, "stage must be 1, 2 or 3");
+    DG_CUDA(rk_stage_launch(m, stage, dt, as_stream(stream)));
     return DG_OK;
 }
 
 dg_status dg_rk3_step(dg_mesh* m, double dt, int nsteps, void* stream) {
     if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
     if (nsteps < 0) return fail(DG_ERR_ARG, "nsteps must be >= 0");
-    for (int n = 0; n < nsteps; ++n)
-        for (int st = 1; st <= 3; ++st) {
-            dg_status r = dg_rk_stage(m, st, dt, stream);
-            if (r != DG_OK) return r;
-        }
+    if (nsteps == 0) return DG_OK;
+    if (!m->has_state) return fail(DG_ERR_NOSTATE, "no state set");
+    if (!(dt >= 0.0)) return fail(DG_ERR_ARG, "dt must be >= 0");
+    cudaStream_t s = as_stream(stream);
+    int n = 0;
+    if (m->host.ne <= GRAPH_MAX_NE && nsteps >= GRAPH_STEPS) {
+        DG_CUDA(rk_graph(m, dt));
+        for (; n + GRAPH_STEPS <= nsteps; n += GRAPH_STEPS) DG_CUDA(cudaGraphLaunch(m->rk_exec, s));
+    }
+    for (; n < nsteps; ++n)
+        for (int st = 1; st <= 3; ++st) DG_CUDA(rk_stage_launch(m, st, dt, s));
     return DG_OK;
 }
 

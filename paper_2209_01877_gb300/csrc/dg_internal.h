@@ -121,6 +121,10 @@ struct dg_mesh {
     double* d_red = nullptr;       // reduction scratch
     double* h_red = nullptr;       // pinned host reduction result
     unsigned int* d_status = nullptr;
+    // small meshes: a CUDA graph of several captured RK3 steps at one dt (dg_rk3_step)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t rk_exec = nullptr;
+    double rk_graph_dt = -1.0;
     size_t state_bytes() const;
 };
 
