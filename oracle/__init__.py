@@ -35,4 +35,7 @@ Parity status per function (what pins it is in tests/test_oracle_*.py):
                        dot-product identity with the VJP
   boundary ghost states pinned: zero wall mass flux, free-stream preservation
                        with boundaries
+  Navier-Stokes lines  pinned (oracle/ns.py): BR1 gradient exact for
+  (BR1, viscous flux)  polynomial states, chain rule vs complex step,
+                       conservation, free stream, shear-wave consistency
 """
