@@ -450,6 +450,8 @@ def run_study(args):
                  multi-step adjoint (steps = --steps, checkpoints every 10).
     aux          the time-step reduction and the conservation / kinetic-energy
                  sums (device time per call).
+    ns           (periodic workloads, FP64) device time of the Navier-Stokes residual
+                 (BR1 gradient and viscous lines added) against the Euler residual.
     launch       device time per RK3 step of dg_rk3_step (a replayed CUDA graph on
                  small meshes) against one dg_rk_stage launch per stage.
     conservation (periodic workloads) change of the conserved totals over
@@ -540,6 +542,30 @@ def run_study(args):
         t_int = (time.perf_counter() - t0) / n
         out.update({"stable_dt_ms_incl_sync": t_dt * 1e3, "integrals_ms_incl_sync": t_int * 1e3,
                     "tets": mesh.ne})
+    elif args.study == "ns":
+        if w["box"]:
+            raise SystemExit("the Navier-Stokes residual needs a periodic workload")
+        M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, None, order=p, precision=dg.DG_FP64, flux=fl)
+        U = torch.from_numpy(M.project(field)).cuda()
+        R = torch.empty_like(U)
+        n = max(args.steps, 3)
+        res = {}
+        calls = (("dg_residual (Euler)", lambda: dg.dg_residual(M.handle, U, R)),
+                 ("dg_ns_residual (mu 1e-3, Pr 0.72)", lambda: dg.dg_ns_residual(M.handle, U, R, 1e-3, 0.72)))
+        for name, call in calls:
+            call()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(n):
+                call()
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3 / n
+            res[name] = {"ms": t * 1e3, "dof_updates_per_s": mesh.ne * 5 * NB[p] / t}
+        dg.dg_sync_status(M.handle)
+        M.close()
+        out.update({"precision": "f64", "tets": mesh.ne, "calls": n, "rows": res})
     elif args.study == "launch":
         prec = {"fp64": dg.DG_FP64, "fp32": dg.DG_FP32, "mixed-bf16": dg.DG_MIXED_BF16}.get(args.precision,
                                                                                          dg.DG_MIXED_FP16)
@@ -631,7 +657,7 @@ def main():
     ap.add_argument("--order", default=None, choices=ORDER_NAMES,
                     help="element order (default: the workload's; RCM for c2, Morton otherwise)")
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 comparison leg of a mixed run")
-    ap.add_argument("--study", choices=["temporal-mp", "renumbering", "adjoint", "aux", "conservation", "launch"],
+    ap.add_argument("--study", choices=["temporal-mp", "renumbering", "adjoint", "aux", "conservation", "launch", "ns"],
                     default=None,
                     help="print a study table instead of the benchmark line")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

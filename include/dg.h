@@ -147,6 +147,18 @@ dg_status dg_get_state(const dg_mesh* mesh, double* U, int on_device, void* stre
  * internal state; R: device FP64 [ne][5][Nb], caller-owned, caller order. */
 dg_status dg_residual(dg_mesh* mesh, const double* U, double* R, void* stream);
 
+/* Navier-Stokes residual (Eq. 1 with ivis = 1, Sec. II-A): the residual of
+ * dg_residual plus Eq. 11's viscous lines in BR1 form (Sec. II-B): the
+ * auxiliary gradient Z = grad Q from central traces, then the viscous volume
+ * term and the central viscous face flux.  Viscous flux of Eq. 1 in 3D with
+ * Stokes' stress, constant viscosity mu >= 0 and Prandtl number prandtl > 0,
+ * gas constant 1 (T = p / rho), conduction coefficient
+ * mu gamma / ((gamma - 1) prandtl).  U and R as for dg_residual (device,
+ * caller order; U NULL = the internal state).  FP64 meshes without boundary
+ * faces only (else DG_ERR_UNSUPPORTED).  The first call with mu > 0 allocates
+ * the gradient buffer (15 Nb doubles per element), owned by the mesh. */
+dg_status dg_ns_residual(dg_mesh* mesh, const double* U, double* R, double mu, double prandtl, void* stream);
+
 /* One SSP-RK3 stage on the internal state, fused with the residual (one
  * kernel launch): stage 1 U1 = U0 + dt R(U0); stage 2 U2 = 3/4 U0 + 1/4 (U1
  * + dt R(U1)); stage 3 U0 <- 1/3 U0 + 2/3 (U2 + dt R(U2)). */

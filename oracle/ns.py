@@ -38,7 +38,7 @@ Parity status: pinned by tests/test_oracle_ns.py:
   * discrete conservation holds on periodic meshes;
   * a uniform state has zero viscous residual;
   * the viscous momentum residual of a shear wave converges to mu d2u/dy2 at order p - 1.
-There is no GPU counterpart yet.
+The CUDA counterpart is dg_ns_residual (FP64); tests/test_gpu_ns.py compares the two.
 """
 from __future__ import annotations
 

@@ -70,6 +70,7 @@ void free_mesh(dg_mesh* m) {
     for (auto& b : m->d_B) cudaFree(b);
     for (auto& b : m->d_V) cudaFree(b);
     cudaFree(m->d_io);
+    cudaFree(m->d_Z);
     if (m->rk_exec) cudaGraphExecDestroy(m->rk_exec);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     cudaFree(m->d_red);
@@ -342,6 +343,30 @@ dg_status dg_residual(dg_mesh* m, const double* U, double* R, void* stream) {
         return DG_OK;
     }
     DG_CUDA(dg::launch_residual(m, in, nullptr, m->d_B[2], 0, 0.0, 0.0, 0.0, s));
+    DG_CUDA(dg::launch_scatter(m, m->d_B[2], R, s));
+    return DG_OK;
+}
+
+dg_status dg_ns_residual(dg_mesh* m, const double* U, double* R, double mu, double prandtl, void* stream) {
+    if (!m || !R) return fail(DG_ERR_ARG, "mesh and R must be non-NULL");
+    if (!(mu >= 0.0) || !(prandtl > 0.0)) return fail(DG_ERR_ARG, "mu must be >= 0 and prandtl > 0");
+    if (m->precision != DG_FP64) return fail(DG_ERR_UNSUPPORTED, "the Navier-Stokes residual runs on FP64 meshes");
+    if (m->host.n_bfaces > 0)
+        return fail(DG_ERR_UNSUPPORTED, "the Navier-Stokes residual needs a mesh without boundary faces");
+    cudaStream_t s = as_stream(stream);
+    const void* in = m->d_B[0];
+    if (U) {
+        DG_CUDA(dg::launch_gather(m, U, m->d_B[1], s));
+        in = m->d_B[1];
+    } else if (!m->has_state) {
+        return fail(DG_ERR_NOSTATE, "no state set and U is NULL");
+    }
+    DG_CUDA(dg::launch_residual(m, in, nullptr, m->d_B[2], 0, 0.0, 0.0, 0.0, s));
+    if (mu > 0.0) {
+        if (!m->d_Z) DG_CUDA(cudaMalloc(&m->d_Z, (size_t)m->host.ne * 15 * m->nb * sizeof(double)));
+        DG_CUDA(dg::launch_ns_viscous(m, static_cast<const double*>(in), m->d_Z, static_cast<double*>(m->d_B[2]), mu,
+                                      prandtl, s));
+    }
     DG_CUDA(dg::launch_scatter(m, m->d_B[2], R, s));
     return DG_OK;
 }

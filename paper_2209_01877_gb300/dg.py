@@ -24,8 +24,8 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_MESH", 3: "DG_ERR_CUDA",
                 5: "DG_ERR_NONPHYSICAL", 6: "DG_ERR_NOSTATE", 7: "DG_ERR_UNSUPPORTED", 8: "DG_ERR_TIMEOUT"}
 
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_element_order", "dg_sizes",
-            "dg_volume_points", "dg_project", "dg_set_state", "dg_get_state", "dg_residual", "dg_rk_stage",
-            "dg_rk3_step", "dg_stable_dt", "dg_integrals", "dg_residual_vjp", "dg_rk3_step_vjp",
+            "dg_volume_points", "dg_project", "dg_set_state", "dg_get_state", "dg_residual", "dg_ns_residual",
+            "dg_rk_stage", "dg_rk3_step", "dg_stable_dt", "dg_integrals", "dg_residual_vjp", "dg_rk3_step_vjp",
             "dg_kinetic_energy_grad", "dg_sync_status", "dg_reference_data", "dg_conserved_totals_noalloc",
             "dg_last_error"]
 
@@ -65,6 +65,7 @@ def load():
             "dg_set_state": [vp, vp, C.c_int, vp],
             "dg_get_state": [vp, vp, C.c_int, vp],
             "dg_residual": [vp, vp, vp, vp],
+            "dg_ns_residual": [vp, vp, vp, C.c_double, C.c_double, vp],
             "dg_rk_stage": [vp, C.c_int, C.c_double, vp],
             "dg_rk3_step": [vp, C.c_double, C.c_int, vp],
             "dg_stable_dt": [vp, C.c_double, C.POINTER(C.c_double), vp],
@@ -212,6 +213,10 @@ def dg_get_state(mesh, U, stream=None):
 
 def dg_residual(mesh, U, R, stream=None):
     _check(load().dg_residual(mesh, _dptr(U), _dptr(R), _stream(stream)))
+
+
+def dg_ns_residual(mesh, U, R, mu, prandtl=0.72, stream=None):
+    _check(load().dg_ns_residual(mesh, _dptr(U), _dptr(R), float(mu), float(prandtl), _stream(stream)))
 
 
 def dg_rk_stage(mesh, stage, dt, stream=None):
