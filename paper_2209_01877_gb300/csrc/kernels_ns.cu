@@ -19,8 +19,6 @@
 //
 // Written for clarity, not speed: the tables are read through the cache, the per-thread
 // accumulators live in local memory.
-#include <algorithm>
-
 #include "dg_internal.h"
 
 namespace dg {
