@@ -81,6 +81,19 @@ def test_argument_errors(lib):
     assert e.value.status == 1
 
 
+def test_null_mesh_is_an_argument_error(lib):
+    """Every entry point that takes a mesh checks it before touching a device."""
+    import ctypes as C
+    null = C.c_void_p(0)
+    buf = C.c_void_p(0)
+    assert lib.dg_ns_residual(null, buf, buf, 0.01, 0.72, null) == 1
+    assert lib.dg_residual(null, buf, buf, null) == 1
+    assert lib.dg_rk3_step(null, 1e-3, 1, null) == 1
+    assert lib.dg_rk_stage(null, 1, 1e-3, null) == 1
+    assert lib.dg_set_state(null, buf, 0, null) == 1
+    assert "NULL" in lib.dg_last_error().decode()
+
+
 def test_mesh_errors(lib):
     m = I.make_periodic_cube(3)
     bad = m.tet_xyz.copy()
