@@ -144,7 +144,12 @@ dg_status dg_get_state(const dg_mesh* mesh, double* U, int on_device, void* stre
 
 /* Residual R = M^-1 (volume - faces) of Eq. 11 (dU/dt of the semi-discrete
  * system).  U: device FP64 [ne][5][Nb] in caller order, or NULL for the
- * internal state; R: device FP64 [ne][5][Nb], caller-owned, caller order. */
+ * internal state; R: device FP64 [ne][5][Nb], caller-owned, caller order.
+ * The first call allocates two work buffers of the state's size, owned by
+ * the mesh (a caller's U in internal order, and R in internal order); they
+ * are apart from the RK stage buffers, so this call, dg_ns_residual and
+ * dg_integrals may come between dg_rk_stage calls without disturbing the
+ * step in progress. */
 dg_status dg_residual(dg_mesh* mesh, const double* U, double* R, void* stream);
 
 /* Navier-Stokes residual (Eq. 1 with ivis = 1, Sec. II-A): the residual of

@@ -69,6 +69,7 @@ void free_mesh(dg_mesh* m) {
     cudaFree(m->d_mxnbr);
     for (auto& b : m->d_B) cudaFree(b);
     for (auto& b : m->d_V) cudaFree(b);
+    for (auto& b : m->d_W) cudaFree(b);
     cudaFree(m->d_io);
     cudaFree(m->d_Z);
     if (m->rk_exec) cudaGraphExecDestroy(m->rk_exec);
@@ -80,6 +81,13 @@ void free_mesh(dg_mesh* m) {
 }
 
 constexpr int RED_SLOTS = 1024 * 6;   // per-block partials; results follow
+
+// the residual / totals work buffers, allocated on first use
+dg_status ensure_work_buffers(dg_mesh* m) {
+    for (auto& b : m->d_W)
+        if (!b) DG_CUDA(cudaMalloc(&b, m->state_bytes() + 256));
+    return DG_OK;
+}
 
 }  // namespace
 
@@ -327,23 +335,24 @@ dg_status dg_get_state(const dg_mesh* mc, double* U, int on_device, void* stream
 
 dg_status dg_residual(dg_mesh* m, const double* U, double* R, void* stream) {
     if (!m || !R) return fail(DG_ERR_ARG, "mesh and R must be non-NULL");
+    if (!U && !m->has_state) return fail(DG_ERR_NOSTATE, "no state set and U is NULL");
+    dg_status st = ensure_work_buffers(m);
+    if (st != DG_OK) return st;
     cudaStream_t s = as_stream(stream);
     const void* in = m->d_B[0];
     if (U) {
-        DG_CUDA(dg::launch_gather(m, U, m->d_B[1], s));
-        in = m->d_B[1];
-    } else if (!m->has_state) {
-        return fail(DG_ERR_NOSTATE, "no state set and U is NULL");
+        DG_CUDA(dg::launch_gather(m, U, m->d_W[0], s));
+        in = m->d_W[0];
     }
     if (is_mixed(m)) {
         const float* hi = static_cast<const float*>(in);
-        float* out = static_cast<float*>(m->d_B[2]);
+        float* out = static_cast<float*>(m->d_W[1]);
         DG_CUDA(dg::launch_residual_mixed(m, hi, nullptr, nullptr, nullptr, out, nullptr, 0, 0.0, 0.0, 0.0, s));
         DG_CUDA(dg::launch_scatter_f32(m, out, R, s));
         return DG_OK;
     }
-    DG_CUDA(dg::launch_residual(m, in, nullptr, m->d_B[2], 0, 0.0, 0.0, 0.0, s));
-    DG_CUDA(dg::launch_scatter(m, m->d_B[2], R, s));
+    DG_CUDA(dg::launch_residual(m, in, nullptr, m->d_W[1], 0, 0.0, 0.0, 0.0, s));
+    DG_CUDA(dg::launch_scatter(m, m->d_W[1], R, s));
     return DG_OK;
 }
 
@@ -353,21 +362,22 @@ dg_status dg_ns_residual(dg_mesh* m, const double* U, double* R, double mu, doub
     if (m->precision != DG_FP64) return fail(DG_ERR_UNSUPPORTED, "the Navier-Stokes residual runs on FP64 meshes");
     if (m->host.n_bfaces > 0)
         return fail(DG_ERR_UNSUPPORTED, "the Navier-Stokes residual needs a mesh without boundary faces");
+    if (!U && !m->has_state) return fail(DG_ERR_NOSTATE, "no state set and U is NULL");
+    dg_status st = ensure_work_buffers(m);
+    if (st != DG_OK) return st;
     cudaStream_t s = as_stream(stream);
     const void* in = m->d_B[0];
     if (U) {
-        DG_CUDA(dg::launch_gather(m, U, m->d_B[1], s));
-        in = m->d_B[1];
-    } else if (!m->has_state) {
-        return fail(DG_ERR_NOSTATE, "no state set and U is NULL");
+        DG_CUDA(dg::launch_gather(m, U, m->d_W[0], s));
+        in = m->d_W[0];
     }
-    DG_CUDA(dg::launch_residual(m, in, nullptr, m->d_B[2], 0, 0.0, 0.0, 0.0, s));
+    DG_CUDA(dg::launch_residual(m, in, nullptr, m->d_W[1], 0, 0.0, 0.0, 0.0, s));
     if (mu > 0.0) {
         if (!m->d_Z) DG_CUDA(cudaMalloc(&m->d_Z, (size_t)m->host.ne * 15 * m->nb * sizeof(double)));
-        DG_CUDA(dg::launch_ns_viscous(m, static_cast<const double*>(in), m->d_Z, static_cast<double*>(m->d_B[2]), mu,
+        DG_CUDA(dg::launch_ns_viscous(m, static_cast<const double*>(in), m->d_Z, static_cast<double*>(m->d_W[1]), mu,
                                       prandtl, s));
     }
-    DG_CUDA(dg::launch_scatter(m, m->d_B[2], R, s));
+    DG_CUDA(dg::launch_scatter(m, m->d_W[1], R, s));
     return DG_OK;
 }
 
@@ -397,13 +407,11 @@ constexpr int64_t GRAPH_MAX_NE = 65536;
 constexpr int GRAPH_STEPS = 8;
 
 // the mesh's graph of GRAPH_STEPS steps at this dt, captured on its private stream when missing
-// or captured at another dt (the buffers and tables it launches on are fixed per mesh)
+// or captured at another dt (the buffers and tables it launches on are fixed per mesh).  A new
+// dt changes only kernel arguments, so the instantiated graph is updated in place
+// (cudaGraphExecUpdate); it is instantiated anew only if that update is refused.
 cudaError_t rk_graph(dg_mesh* m, double dt) {
     if (m->rk_exec && m->rk_graph_dt == dt) return cudaSuccess;
-    if (m->rk_exec) {
-        cudaGraphExecDestroy(m->rk_exec);
-        m->rk_exec = nullptr;
-    }
     cudaError_t e = cudaSuccess;
     if (!m->cap_stream) e = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
@@ -415,10 +423,20 @@ cudaError_t rk_graph(dg_mesh* m, double dt) {
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(m->cap_stream, &g);
     if (el != cudaSuccess) e = el;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&m->rk_exec, g, 0);
+    if (e == cudaSuccess && m->rk_exec) {
+        cudaGraphExecUpdateResultInfo info{};
+        if (cudaGraphExecUpdate(m->rk_exec, g, &info) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaGraphExecDestroy(m->rk_exec);
+            m->rk_exec = nullptr;
+        }
+    }
+    if (e == cudaSuccess && !m->rk_exec) e = cudaGraphInstantiate(&m->rk_exec, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) {
+        if (m->rk_exec) cudaGraphExecDestroy(m->rk_exec);
         m->rk_exec = nullptr;
+        m->rk_graph_dt = -1.0;
         return e;
     }
     m->rk_graph_dt = dt;
@@ -467,13 +485,14 @@ dg_status dg_stable_dt(dg_mesh* m, double cfl, double* dt_host, void* stream) {
 
 dg_status dg_integrals(dg_mesh* m, const double* U, double totals[5], double* ke, void* stream) {
     if (!m || !totals) return fail(DG_ERR_ARG, "mesh and totals must be non-NULL");
+    if (!U && !m->has_state) return fail(DG_ERR_NOSTATE, "no state set and U is NULL");
     cudaStream_t s = as_stream(stream);
     const void* in = m->d_B[0];
     if (U) {
-        DG_CUDA(dg::launch_gather(m, U, m->d_B[1], s));
-        in = m->d_B[1];
-    } else if (!m->has_state) {
-        return fail(DG_ERR_NOSTATE, "no state set and U is NULL");
+        dg_status st = ensure_work_buffers(m);
+        if (st != DG_OK) return st;
+        DG_CUDA(dg::launch_gather(m, U, m->d_W[0], s));
+        in = m->d_W[0];
     }
     double* d_out = m->d_red + RED_SLOTS;
     DG_CUDA(dg::launch_integrals(m, in, d_out, s));

@@ -8,35 +8,9 @@
 #include <cuda_runtime.h>
 
 #include "../../include/dg.h"
+#include "dg_device.h"
 
 namespace dg {
-
-// Sizes per polynomial order p (1..3): modes, volume points (symmetric rule
-// exact to degree 2p), face points (symmetric triangle rule exact to 2p).
-constexpr int nb_of(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
-constexpr int nq_of(int p) { return p == 1 ? 4 : (p == 2 ? 14 : 24); }
-constexpr int nqf_of(int p) { return p == 1 ? 3 : (p == 2 ? 6 : 12); }
-
-// Offsets (in elements of the table's scalar type) of the basis tables,
-// stored contiguously so a kernel can stage them into shared memory at once:
-//   PHIQ  [Nb][Nq]      phi_j at volume point q
-//   DPHIW [3][Nq][Nb]   w_q * d phi_j / d xi_k at volume point q
-//   PHIF  [4][Nb][Nqf]  phi_j at point q of local face f (own point order)
-//   PHIFW [4][Nqf][Nb]  wf_q * phi_j at point q of local face f
-//   WQ    [Nq]          volume weights (sum 1/6)
-struct TabLayout {
-    int nb, nq, nqf;
-    int phiq, dphiw, phif, phifw, wq, total;
-    explicit TabLayout(int p) {
-        nb = nb_of(p); nq = nq_of(p); nqf = nqf_of(p);
-        phiq = 0;
-        dphiw = phiq + nb * nq;
-        phif = dphiw + 3 * nq * nb;
-        phifw = phif + 4 * nb * nqf;
-        wq = phifw + 4 * nqf * nb;
-        total = wq + nq;
-    }
-};
 
 // Host-built reference data (FP64): quadrature, basis tables and the face
 // point permutations for the 6 relative orientations.
@@ -72,24 +46,6 @@ bool build_mesh(const int32_t* tet_vid, const double* tet_xyz, const int8_t* bc_
 
 }  // namespace dg
 
-// Device-side arguments of the residual / RK-stage kernel.
-template <typename Real>
-struct ResArgs {
-    const Real* U;         // residual input [ne][5][Nb] internal order
-    const Real* U0;        // RK base state (stages 2, 3)
-    Real* out;             // residual or new state
-    const int32_t* nbr;    // [ne][4]
-    const uint8_t* fcode;  // [ne][4]
-    const Real* jinv;      // [ne][9]
-    const Real* tab;       // basis tables (TabLayout)
-    const int8_t* fperm;   // [6][Nqf]
-    int64_t ne;
-    Real dt, a, b;         // out = a*U0 + b*(U + dt*R) in RK mode
-    Real gamma, roe_eps;
-    Real finf[5];          // free-stream conserved state
-    unsigned int* status;  // device status word
-};
-
 struct dg_mesh {
     int p = 1, nb = 4, nq = 4, nqf = 3;
     int precision = DG_FP64, flux = DG_RUSANOV;
@@ -117,6 +73,9 @@ struct dg_mesh {
     int32_t* d_mxnbr = nullptr;
     void* d_B[3] = {nullptr, nullptr, nullptr};   // state buffers (internal precision)
     void* d_V[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // adjoint work buffers (lazy)
+    // residual / totals work buffers (lazy): a caller's state in internal order, and the residual
+    // in internal order; kept apart from d_B so these calls never touch an RK step in progress
+    void* d_W[2] = {nullptr, nullptr};
     double* d_io = nullptr;        // FP64 [ne][5][Nb] staging for host copies
     double* d_red = nullptr;       // reduction scratch
     double* h_red = nullptr;       // pinned host reduction result

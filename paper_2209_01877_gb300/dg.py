@@ -268,10 +268,22 @@ def dg_reference_data(order):
     return out
 
 
+NOALLOC_MAX_NE = 4194304   # capacity of the library's fixed scratch array
+
+
 def dg_conserved_totals_noalloc(U, detJ, totals, stream=None, ne=None):
     """Allocation-free conserved totals: U [ne][5][nb], detJ [ne], totals [5],
-    all float64 CUDA tensors owned by the caller."""
+    all float64 CUDA tensors owned by the caller.  ``ne`` defaults to
+    U.shape[0]; a smaller ne sums the first ne elements.  An ne above the
+    tensors' sizes is refused here, except beyond the library's capacity
+    (NOALLOC_MAX_NE), where the library itself rejects it before any launch."""
     n = int(U.shape[0]) if ne is None else int(ne)
+    if U.dim() != 3 or U.shape[1] != 5:
+        raise ValueError("U must be [ne][5][nb]")
+    if totals.numel() < 5:
+        raise ValueError("totals must hold 5 values")
+    if n <= NOALLOC_MAX_NE and (n > U.shape[0] or n > detJ.numel()):
+        raise ValueError(f"ne={n} exceeds U ({U.shape[0]} elements) or detJ ({detJ.numel()} values)")
     _check(load().dg_conserved_totals_noalloc(_dptr(U), _dptr(detJ), n, int(U.shape[2]), _dptr(totals),
                                               _stream(stream)))
 

@@ -33,6 +33,7 @@ from gpu_helpers import (gpu_residual, make_mesh, max_rel_err, residual_term_sca
 pytestmark = pytest.mark.gpu
 TOL64 = 1e-12
 TOL32 = 1e-4
+PLAIN_BOX = 1e-10
 
 
 def _box(nx=4, ny=3, nz=3):
@@ -49,20 +50,34 @@ def _box_state(P):
     return P.project(field)
 
 
+def _both_bars(got, ref, P, U):
+    """(plain, term-scaled) relative errors: max|dR_Q| / max|R_Q| and
+    max|dR_Q| / max(max|R_Q|, S_Q), per conserved quantity Q."""
+    return max_rel_err(got, ref), max_rel_err(got, ref, term_scale=residual_term_scale(P, U))
+
+
 @pytest.mark.parametrize("p", [1, 2, 3])
 @pytest.mark.parametrize("flux", ["rusanov", "roe"])
 def test_residual_periodic_fp64(p, flux):
+    """The vortex fills the cube, so the residual is nowhere pure cancellation and
+    the plain bar (no term-scale floor) holds as well."""
     m = I.make_periodic_cube(4, jitter=0.15)
     P = Problem(m.tet_vid, m.tet_xyz, None, p=p, flux=flux)
     U = vortex_state(P, radius=0.15)
     R = P.residual(U)
     M = make_mesh(m, p, flux)
-    assert max_rel_err(gpu_residual(M, U), R, term_scale=residual_term_scale(P, U)) < TOL64
+    plain, floored = _both_bars(gpu_residual(M, U), R, P, U)
+    print(f"periodic p={p} {flux}: plain {plain:.2e}, term-scaled {floored:.2e}")
+    assert floored < TOL64
+    assert plain < TOL64
 
 
 @pytest.mark.parametrize("p", [1, 2, 3])
 @pytest.mark.parametrize("flux", ["rusanov", "roe"])
 def test_residual_box_boundaries_fp64(p, flux):
+    """A pulse in a channel: away from the pulse the residual is free-stream
+    cancellation, so the term-scale floor is what the 1e-12 bar rests on; the
+    plain error is held to PLAIN_BOX (measured on GB300, with margin)."""
     m = _box()
     Uinf = I.freestream_state(0.3)
     P = Problem(m.tet_vid, m.tet_xyz, m.bc_tag, p=p, flux=flux, freestream=Uinf)
@@ -70,7 +85,10 @@ def test_residual_box_boundaries_fp64(p, flux):
     R = P.residual(U)
     M = make_mesh(m, p, flux, freestream=Uinf)
     assert M.info()["n_bfaces"] == 4 * (3 * 3 + 4 * 3 + 4 * 3)
-    assert max_rel_err(gpu_residual(M, U), R, term_scale=residual_term_scale(P, U)) < TOL64
+    plain, floored = _both_bars(gpu_residual(M, U), R, P, U)
+    print(f"box p={p} {flux}: plain {plain:.2e}, term-scaled {floored:.2e}")
+    assert floored < TOL64
+    assert plain < PLAIN_BOX
 
 
 @pytest.mark.parametrize("p", [1, 3])
@@ -103,16 +121,36 @@ def test_renumbering_is_a_permutation():
 
 
 def test_free_stream_and_conservation_gpu():
+    """Free stream on the jittered periodic mesh: the weak-form residual M R =
+    |det J| R (orthonormal basis) is at most 1e-13, the bar the oracle's own
+    free-stream pin uses; then discrete conservation of the vortex residual."""
     m = I.make_periodic_cube(4, jitter=0.15)
     for p in (1, 2, 3):
         P = Problem(m.tet_vid, m.tet_xyz, None, p=p)
         M = make_mesh(m, p, "roe")
         R = gpu_residual(M, P.project(I.uniform_flow))
-        assert np.abs(R).max() < 1e-11
+        weak = R * P.det[:, None, None]
+        print(f"free stream p={p}: max weak-form residual {np.abs(weak).max():.2e}")
+        assert np.abs(weak).max() < 1e-13
         R = gpu_residual(M, vortex_state(P, radius=0.15))
         rate = np.einsum("e,ev->v", P.det, R[:, :, 0]) * math.sqrt(6.0) / 6.0
         scale = np.einsum("e,ev->v", P.det, np.abs(R[:, :, 0]))
         assert np.all(np.abs(rate) < 1e-13 * scale)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_free_stream_with_boundaries_gpu(precision):
+    """Uniform free stream through a channel with slip walls and far-field faces:
+    weak-form residual <= 1e-13 (FP64), or FP32 round-off of the term scale."""
+    m = _box()
+    Uinf = I.freestream_state(0.3)
+    P = Problem(m.tet_vid, m.tet_xyz, m.bc_tag, p=2, flux="roe", freestream=Uinf)
+    U = P.project(lambda x: np.broadcast_to(Uinf, x.shape[:-1] + (5,)).copy())
+    M = make_mesh(m, 2, "roe", precision=precision, freestream=Uinf)
+    weak = gpu_residual(M, U) * P.det[:, None, None]
+    bar = 1e-13 if precision == "fp64" else 1e-4 * max(residual_term_scale(P, U)) * P.det.max()
+    print(f"free stream with boundaries {precision}: max weak-form residual {np.abs(weak).max():.2e}")
+    assert np.abs(weak).max() < bar
 
 
 def test_config1_one_rk3_step():
@@ -186,6 +224,36 @@ def test_rk3_step_graph_replay_matches_stage_launches(precision):
         dg.dg_sync_status(Mg.handle)
         np.testing.assert_array_equal(ug, ul)
     assert np.abs(ug - U0).max() > 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_residual_and_totals_calls_between_stages_leave_the_step_intact(precision):
+    """dg_residual and dg_integrals (with a caller state or the internal one) called between
+    the stages of an SSP-RK3 step use their own work buffers: the step ends bit-identical to
+    the same stages launched without them."""
+    torch = torch_cuda()
+    m = I.make_periodic_cube(4, jitter=0.15)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=2)
+    U0 = vortex_state(P, radius=0.2)
+    other = torch.from_numpy(P.project(I.uniform_flow)).cuda()
+    R = torch.empty_like(other)
+    Ma = make_mesh(m, 2, "roe", precision=precision, renumber=dg.DG_ORDER_MORTON)
+    Mb = make_mesh(m, 2, "roe", precision=precision, renumber=dg.DG_ORDER_MORTON)
+    dg.dg_set_state(Ma.handle, U0)
+    dg.dg_set_state(Mb.handle, U0)
+    dt = dg.dg_stable_dt(Ma.handle, 0.1)
+    for st in (1, 2, 3):
+        dg.dg_rk_stage(Ma.handle, st, dt)
+        dg.dg_rk_stage(Mb.handle, st, dt)
+        dg.dg_residual(Mb.handle, other, R)
+        dg.dg_residual(Mb.handle, None, R)
+        dg.dg_integrals(Mb.handle, other)
+        dg.dg_integrals(Mb.handle)
+    ua, ub = np.empty_like(U0), np.empty_like(U0)
+    dg.dg_get_state(Ma.handle, ua)
+    dg.dg_get_state(Mb.handle, ub)
+    dg.dg_sync_status(Mb.handle)
+    np.testing.assert_array_equal(ua, ub)
 
 
 def test_state_roundtrip_and_integrals():

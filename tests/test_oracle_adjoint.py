@@ -82,3 +82,62 @@ def test_kinetic_energy_gradient():
     ke = 0.5 * np.sum(Uq[..., 1:4] ** 2, axis=-1) / Uq[..., 0]
     dke = np.imag(np.einsum("q,e,eq->", P.wq, P.det, ke)) / h
     assert abs(np.sum(P.kinetic_energy_grad(U) * v) - dke) < 1e-13 * abs(dke)
+
+
+def _rk3_adjoint_dot(P, U0, dt, nsteps, lam, v, adjoint=None):
+    """(<lam, d U_n / d U_0 v> by complex step, <rk3_adjoint(lam), v>)."""
+    h = 1e-30
+    Un = P.rk3(U0.astype(complex) + 1j * h * v, dt, nsteps)
+    cs = float(np.sum(lam * np.imag(Un)) / h)
+    adj = (adjoint or P.rk3_adjoint)(U0, dt, nsteps, lam)
+    return cs, float(np.sum(adj * v))
+
+
+def _adjoint_case(flux):
+    m = I.make_periodic_cube(3, jitter=0.15)
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=1, flux=flux)
+    U0 = P.project(lambda x: I.isentropic_vortex(x, radius=0.2))
+    # a time step large enough that the stored states differ visibly from step to step
+    dt = P.stable_dt(U0, 0.4)
+    lam, v = I.random_directions(U0.shape, 2, seed=41)
+    return P, U0, dt, lam, v
+
+
+@pytest.mark.parametrize("flux", ["rusanov", "roe"])
+@pytest.mark.parametrize("nsteps", [3, 4])
+def test_rk3_adjoint_vs_complex_step(flux, nsteps):
+    """Reverse sweep over n stored SSP-RK3 steps (Sec. III's explicit scheme):
+    <rk3_adjoint(lam), v> equals the complex-step derivative of
+    <lam, rk3^n(U0 + i h v)> to 1e-12 relative."""
+    P, U0, dt, lam, v = _adjoint_case(flux)
+    cs, adj = _rk3_adjoint_dot(P, U0, dt, nsteps, lam, v)
+    assert abs(cs - adj) < 1e-12 * abs(cs), (cs, adj)
+
+
+def test_rk3_adjoint_pin_catches_state_order_mistakes():
+    """Planted in a copy of the oracle on the CPU: reversing each step about
+    the next step's start state (off by one) or sweeping the steps forwards
+    instead of backwards must fail the complex-step pin above."""
+    P, U0, dt, lam, v = _adjoint_case("roe")
+
+    def off_by_one(U0_, dt_, n, lam_):
+        states = [np.asarray(U0_, dtype=np.float64)]
+        for _ in range(n):
+            states.append(P.rk3_step(states[-1], dt_))
+        out = lam_
+        for k in reversed(range(n)):
+            out = P.rk3_step_vjp(states[k + 1], dt_, out)
+        return out
+
+    def forward_sweep(U0_, dt_, n, lam_):
+        states = [np.asarray(U0_, dtype=np.float64)]
+        for _ in range(n - 1):
+            states.append(P.rk3_step(states[-1], dt_))
+        out = lam_
+        for k in range(n):
+            out = P.rk3_step_vjp(states[k], dt_, out)
+        return out
+
+    for broken in (off_by_one, forward_sweep):
+        cs, adj = _rk3_adjoint_dot(P, U0, dt, 3, lam, v, adjoint=broken)
+        assert abs(cs - adj) > 1e-9 * abs(cs), broken.__name__
