@@ -127,7 +127,7 @@ MEASURED_TRAFFIC = {
     # (precision, p, flux): (bytes per element per launch, source files, sha256[:16] of them)
     ("mixed", 3, "roe"): (2039.3, ("kernels_mixed.cu", "tc_ops.cuh", "euler_device.cuh", "dg_device.h"),
                           "unmeasured"),
-    ("f64", 3, "roe"): (2072.8, ("kernels_simt.cu", "euler_device.cuh", "dg_device.h"), "unmeasured"),
+    ("f64", 3, "roe"): (2073.7, ("kernels_simt.cu", "euler_device.cuh", "dg_device.h"), "8a8a7d548dc56a5b"),
 }
 
 
@@ -347,75 +347,160 @@ def run_ours(args, rank, world, device):
 
 
 # ---------------------------------------------------------------------------------------------
-def oracle_sample_rate(workload, nsample, reps=1, seed=11, warmup=0, flux=None):
-    """The FP64 oracle's residual on a seeded sample of the workload's
-    elements: (DOF-updates/s averaged over ``reps`` timed evaluations, seconds
-    per evaluation, sample size, per-evaluation rates)."""
+def _field_of(name, w):
+    """The workload's pointwise initial field (the 1% noise of c2 acts on coefficients, not on
+    the field, and does not change the oracle's work)."""
+    from paper_2209_01877_gb300 import inputs as I
+    if name == "pulse":
+        c = I.pulse_centre()
+        return lambda x: I.gaussian_pulse(x, c)
+    return lambda x: I.isentropic_vortex(x)
+
+
+def _oracle_worker(conn, vid, xyz, tag, rows, p, flux, fs, field_name):
+    """One host core: the oracle's residual of `rows` of a sub-mesh (the rows and their face
+    neighbours; faces that lose their partner there get a wall tag -- their elements' residuals
+    are not evaluated).  Answers each message k with the seconds of k back-to-back evaluations."""
     from oracle.dg import Problem
-    mesh, field, w = make_workload(workload)
-    fs = None
-    if w["box"]:
-        from paper_2209_01877_gb300 import inputs as I
-        fs = I.freestream_state(0.3)
-    P = Problem(mesh.tet_vid, mesh.tet_xyz, mesh.bc_tag if w["box"] else None, p=w["p"], flux=flux or w["flux"],
-                freestream=fs)
-    rng = np.random.default_rng(seed)
-    rows = np.sort(rng.choice(mesh.ne, size=min(nsample, mesh.ne), replace=False))
-    need = np.unique(np.concatenate([rows, P.nbr[rows].ravel()]))
-    need = need[need >= 0]
-    U = np.zeros((mesh.ne, 5, P.nb))
-    sub = P.project(field, rule="volume", elems=need)
-    U[need] = sub
+    P = Problem(vid, xyz, tag, p=p, flux=flux, freestream=fs)
+    U = P.project(_field_of(field_name, None), rule="volume")
     P.residual(U, rows[:16])
-    for _ in range(warmup):
-        P.residual(U, rows)
-    rates = []
-    for _ in range(reps):
+    conn.send("ready")
+    while True:
+        k = conn.recv()
+        if k is None:
+            break
         t0 = time.perf_counter()
-        P.residual(U, rows)
-        rates.append(len(rows) * 5 * P.nb / (time.perf_counter() - t0))
-    dt = len(rows) * 5 * P.nb / float(np.mean(rates))
-    return float(np.mean(rates)), dt, len(rows), rates
+        for _ in range(k):
+            P.residual(U, rows)
+        conn.send(time.perf_counter() - t0)
+    conn.close()
 
 
-def _oracle_child(workload, nsample, reps, warmup=0, flux=None):
-    """Run oracle_sample_rate in a child process pinned to one BLAS/OpenMP thread."""
+class OraclePool:
+    """`cores` processes (spawn), each holding an equal share of a seeded sample of the workload's
+    elements; `run(k)` has every process evaluate its share k times at once and returns the wall
+    time until the last one is done."""
+
+    def __init__(self, workload, nsample, cores, flux=None, seed=11):
+        import multiprocessing as mp
+        from oracle.mesh import match_faces
+        mesh, _, w = make_workload(workload)
+        tag = mesh.bc_tag if w["box"] else None
+        nbr, _, _ = match_faces(mesh.tet_vid, tag)
+        rng = np.random.default_rng(seed)
+        rows = np.sort(rng.choice(mesh.ne, size=min(nsample, mesh.ne), replace=False))
+        fs = None
+        if w["box"]:
+            from paper_2209_01877_gb300 import inputs as I
+            fs = I.freestream_state(0.3)
+        self.nrows, self.nb, self.cores = len(rows), NB[w["p"]], cores
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for chunk in np.array_split(rows, cores):
+            need = np.unique(np.concatenate([chunk, nbr[chunk].ravel()]))
+            need = need[need >= 0]
+            t = np.ones((len(need), 4), dtype=np.int8)
+            if w["box"]:
+                t = np.where(mesh.bc_tag[need] > 0, mesh.bc_tag[need], 1).astype(np.int8)
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_oracle_worker, args=(b, mesh.tet_vid[need], mesh.tet_xyz[need], t,
+                                                          np.searchsorted(need, chunk), w["p"],
+                                                          flux or w["flux"], fs, w["field"]))
+            pr.start()
+            self.conns.append(a)
+            self.procs.append(pr)
+        for c in self.conns:
+            assert c.recv() == "ready"
+
+    def run(self, k):
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send(k)
+        for c in self.conns:
+            c.recv()
+        return time.perf_counter() - t0
+
+    def dual_phase_rate(self):
+        """DOF-updates/s from the dual-phase timing (K1 = 1 and K2 = 3 evaluations, subtracted):
+        per-evaluation time without the fixed costs of a call."""
+        t1 = self.run(1)
+        t3 = self.run(3)
+        per = max((t3 - t1) / 2.0, 1e-9)
+        return self.nrows * 5 * self.nb / per, per
+
+    def close(self):
+        for c in self.conns:
+            c.send(None)
+        for pr in self.procs:
+            pr.join(timeout=30)
+
+
+def _oracle_child(mode, workload, nsample, steps=1, warmup=0, flux=None):
+    """Run the oracle timing in a child process (no CUDA device, one BLAS thread per process)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "r = bench.oracle_sample_rate(%r, %d, %d, warmup=%d, flux=%r); print(json.dumps(r))"
-            % (ROOT, workload, nsample, reps, warmup, flux))
+            "print(json.dumps(bench.oracle_timing(%r, %r, %d, %d, %d, %r)))"
+            % (ROOT, mode, workload, nsample, steps, warmup, flux))
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline_subprocess(workload, nsample, reps=1, flux=None):
-    rate, sec, n, _ = _oracle_child(workload, nsample, reps, flux=flux)
-    return {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle residual on {n} seeded elements of {workload} (with their neighbours' "
-                      f"states), {reps} evaluation(s), {sec:.1f}s each, 1 thread"}
+def oracle_timing(mode, workload, nsample, steps=1, warmup=0, flux=None):
+    """mode "baseline": dual-phase rates of the oracle on one core and on every host core;
+    mode "steps": `warmup` untimed and `steps` timed evaluations of the sample on every core."""
+    cores = os.cpu_count() or 1
+    if mode == "baseline":
+        one = OraclePool(workload, nsample, 1, flux)
+        r1, s1 = one.dual_phase_rate()
+        one.close()
+        pool = OraclePool(workload, nsample, cores, flux)
+        rn, sn = pool.dual_phase_rate()
+        pool.close()
+        return {"single": r1, "single_s": s1, "all": rn, "all_s": sn, "cores": cores, "rows": pool.nrows}
+    pool = OraclePool(workload, nsample, cores, flux)
+    for _ in range(warmup):
+        pool.run(1)
+    ts = [pool.run(1) for _ in range(steps)]
+    pool.close()
+    return {"rates": [pool.nrows * 5 * pool.nb / t for t in ts], "seconds": ts, "cores": cores,
+            "rows": pool.nrows}
+
+
+def cpu_baseline_subprocess(workload, nsample, flux=None):
+    r = _oracle_child("baseline", workload, nsample, flux=flux)
+    return {"value": r["all"], "unit": "DOF-updates/s", "cores": r["cores"], "kind": "oracle",
+            "sample": f"FP64 oracle residual on {r['rows']} seeded elements of {workload} (each host process "
+                      f"holds its share and their face neighbours), split over {r['cores']} processes with one "
+                      f"BLAS thread each, dual-phase timing (K1 = 1, K2 = 3 evaluations): {r['all_s']:.2f} s "
+                      f"per evaluation",
+            "single_core": {"value": r["single"], "cores": 1,
+                            "sample": f"the same sample in one process, dual-phase: {r['single_s']:.1f} s per "
+                                      f"evaluation"}}
 
 
 SAMPLE = {"c1": 1296, "c2": 120000, "c3": 60000, "c4": 120000, "c5": 60000, "c3s": 60000}
 
 
 def run_reference(args):
-    """--impl reference: the FP64 oracle on the host, one thread, each step one
-    residual evaluation of a bounded seeded sample of the workload."""
+    """--impl reference: the FP64 oracle on the host cores (one process per core, one BLAS
+    thread each), each step one residual evaluation of a bounded seeded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     cfg = config_of(args)
-    n = max(200, SAMPLE.get(args.workload, 2000) // 3)
-    rate, sec, nrows, rates = _oracle_child(args.workload, n, args.steps, warmup=args.warmup, flux=flux_of(args))
+    n = SAMPLE.get(args.workload, 2000)
+    r = _oracle_child("steps", args.workload, n, args.steps, args.warmup, flux_of(args))
+    rate = float(np.mean(r["rates"]))
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "DOF-updates/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
-            "dtype": "f64", "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"FP64 oracle residual on {nrows} seeded elements of {args.workload} "
-                                       f"per step, 1 thread"},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(r["seconds"])) * 1e3,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": rate, "unit": "DOF-updates/s", "cores": r["cores"], "kind": "oracle",
+                             "sample": f"FP64 oracle residual on {r['rows']} seeded elements of {args.workload} "
+                                       f"per step, split over {r['cores']} processes with one BLAS thread each"},
             "e2e": {"value": rate, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -455,10 +540,10 @@ def run_study(args):
                  (BR1 gradient and viscous lines added) against the Euler residual.
     launch       device time per RK3 step of dg_rk3_step (a replayed CUDA graph on
                  small meshes) against one dg_rk_stage launch per stage.
-    conservation (periodic workloads) change of the conserved totals over
-                 --steps SSP-RK3 steps (FP64 capped at 50) for FP64 and both
-                 mixed forms: with no boundary flux it is the discrete
-                 conservation drift itself."""
+    conservation change of the conserved totals over --steps SSP-RK3 steps
+                 for FP64 and both mixed forms, minus what the boundary flux
+                 carried out (Eq. 11's boundary-face line integrated over the
+                 RK stages): the discrete conservation drift."""
     import torch
     from paper_2209_01877_gb300 import dg
     from paper_2209_01877_gb300.temporal import run_temporal_mp
@@ -596,29 +681,44 @@ def run_study(args):
         out.update({"steps": n, "tets": mesh.ne, "us_per_step": res,
                     "note": "dg_rk3_step replays a CUDA graph of 8 captured steps on meshes of <= 65536 tets"})
     elif args.study == "conservation":
-        if w["box"]:
-            raise SystemExit("the conservation study needs a periodic workload (no boundary flux)")
         ren = {"morton": dg.DG_ORDER_MORTON, "hilbert": dg.DG_ORDER_HILBERT, "rcm": dg.DG_ORDER_RCM,
                "asis": dg.DG_ORDER_ASIS}[order_of(args)]
         rows = []
         for pname, prec in (("f64", dg.DG_FP64), ("f16x2-tc/f32/ff32", dg.DG_MIXED_FP16),
                             ("bf16x2-tc/f32/ff32", dg.DG_MIXED_BF16)):
-            nsteps = min(args.steps, 50) if prec == dg.DG_FP64 else args.steps
-            M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, None, order=p, precision=prec, flux=fl, renumber=ren)
+            nsteps = args.steps
+            M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, tag, order=p, precision=prec, flux=fl, renumber=ren,
+                        freestream=fs)
             dg.dg_set_state(M.handle, M.project(field))
             t0, _ = dg.dg_integrals(M.handle)
             dt = dg.dg_stable_dt(M.handle, 0.1)
-            dg.dg_rk3_step(M.handle, dt, nsteps)
+            acc = np.zeros(5)
+            t_start = time.perf_counter()
+            for _ in range(nsteps):
+                if w["box"]:
+                    # B at the three stage states: the totals move by -dt (B0/6 + B1/6 + 2 B2/3)
+                    b0 = dg.dg_boundary_flux(M.handle)
+                    dg.dg_rk_stage(M.handle, 1, dt)
+                    b1 = dg.dg_boundary_flux(M.handle, None, 1)
+                    dg.dg_rk_stage(M.handle, 2, dt)
+                    b2 = dg.dg_boundary_flux(M.handle, None, 2)
+                    dg.dg_rk_stage(M.handle, 3, dt)
+                    acc += dt * (b0 / 6.0 + b1 / 6.0 + 2.0 * b2 / 3.0)
+                else:
+                    dg.dg_rk3_step(M.handle, dt, 1)
             t1, _ = dg.dg_integrals(M.handle)
             dg.dg_sync_status(M.handle)
             M.close()
-            d = t1 - t0
-            rows.append({"precision": pname, "steps": nsteps, "dt": dt, "totals_start": t0.tolist(),
+            d = t1 - t0 + acc
+            rows.append({"precision": pname, "steps": nsteps, "dt": dt, "seconds": time.perf_counter() - t_start,
+                         "totals_start": t0.tolist(), "boundary_flux_integral": (-acc).tolist(),
                          "drift": d.tolist(),
                          "rel_drift_mass": abs(d[0]) / abs(t0[0]),
                          "rel_drift_momentum": float(np.linalg.norm(d[1:4]) / np.linalg.norm(t0[1:4])),
                          "rel_drift_energy": abs(d[4]) / abs(t0[4])})
-        out.update({"rows": rows, "note": "periodic domain: the change of the totals is the drift itself"})
+        out.update({"rows": rows,
+                    "note": "drift = change of the totals + dt sum over steps of (B0/6 + B1/6 + 2 B2/3), B the "
+                            "boundary-flux integral at the stage states (0 on periodic meshes)"})
     else:
         rows = []
         for name, order in (("input (random)", dg.DG_ORDER_ASIS), ("RCM", dg.DG_ORDER_RCM),
@@ -686,8 +786,7 @@ def main():
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu_base = cpu_baseline_subprocess(args.workload, SAMPLE.get(args.workload, 20000), reps=2,
-                                               flux=flux_of(args))
+            cpu_base = cpu_baseline_subprocess(args.workload, SAMPLE.get(args.workload, 20000), flux=flux_of(args))
         except Exception as e:  # reported, not fatal
             cpu_base = {"value": None, "error": str(e)[-300:]}
     r = run_ours(args, rank, world, device)

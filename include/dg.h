@@ -183,6 +183,21 @@ dg_status dg_stable_dt(dg_mesh* mesh, double cfl, double* dt_host, void* stream)
 dg_status dg_integrals(dg_mesh* mesh, const double* U, double totals[5], double* kinetic_energy,
                        void* stream);
 
+/* Boundary-flux integral B_v = sum over boundary faces f of int_f H_v(Q-, Q_b, n) dS, the
+ * boundary-face line of Eq. 11 with the constant test function: interior fluxes cancel in
+ * pairs, so d/dt int U_v dx = -B_v (Sec. II-B: slip-wall and far-field ghost states through the
+ * numerical flux).  FP64 in every precision (the stored state read as FP64, FP32 or the
+ * float-float pair), fixed-order two-pass sum.  Over one SSP-RK3 step of size dt the totals
+ * change by -dt (B(U0)/6 + B(U1)/6 + 2 B(U2)/3), which is how a run with boundaries checks
+ * its conservation.
+ *   U      device FP64 [ne][5][Nb] in caller order, or NULL for an internal state:
+ *   stage  (with U NULL) 0 = the current state; 1, 2 = the intermediate states U1, U2 that
+ *          dg_rk_stage stages 1 and 2 leave (valid until the next stage call);
+ *   out    host double[5], written.
+ * A mesh without boundary faces gives 0.  Synchronises the stream.  Errors: DG_ERR_ARG,
+ * DG_ERR_NOSTATE, DG_ERR_CUDA, DG_ERR_OOM (first call with U: the work buffers). */
+dg_status dg_boundary_flux(dg_mesh* mesh, const double* U, int stage, double out[5], void* stream);
+
 /* Vector-Jacobian product out = (dR/dU)^T lambda of dg_residual at U (the
  * paper has no adjoint; this reverses the steps of Eq. 11's discretisation:
  * inverse mass, projection, pointwise flux and Riemann-solver Jacobians,
@@ -236,6 +251,57 @@ dg_status dg_reference_data(int order, double* vol_xi, double* vol_w, double* fa
  * Asynchronous on `stream`. */
 dg_status dg_conserved_totals_noalloc(const double* U, const double* detJ, int64_t ne, int nb, double* totals,
                                       void* stream);
+
+/* ---- Element partitions (the layout of a multi-process run) ------------------------------------
+ * The paper renumbers its grid once before time stepping, for every process (Sec. III-B).  A
+ * partitioned run gives partition r a contiguous slab of the renumbered element order (RCM, Morton
+ * or Hilbert keep slabs spatially compact), slab boundaries on multiples of 12 elements (the tile of
+ * the mixed-precision kernel), and a halo: the ascending list of other partitions' elements that its
+ * own elements' faces reach.  One residual evaluation needs one halo exchange; the time-step minimum
+ * and the conserved totals are reduced over the partitions.  Here the k partitions live on the
+ * mesh's device: the exchange is a device gather from the owning partitions' state buffers into each
+ * local halo buffer (what a multi-GPU run does by peer copy or NCCL send/recv into the same local
+ * buffer), and every kernel then reads local memory only. */
+typedef struct dg_partition dg_partition;   /* opaque; owns its local meshes' device buffers */
+
+/* Host only (no device is touched): the plan of partition r of k for a mesh built from these
+ * arrays with this renumbering (the same validation, matching and renumbering as dg_mesh_create).
+ *   first, count: the own slab [first, first + count) of internal element ids;
+ *   nhalo: the halo size; halo_ids [nhalo] (ascending internal ids) and halo_part [nhalo] (the
+ *   owning partition of each), both host, caller-sized, may be NULL (call first with NULL to get
+ *   nhalo).  Any output may be NULL.
+ * Errors: DG_ERR_ARG (bad sizes, r outside [0, k), k too large for a 12-element tile per slab),
+ * DG_ERR_MESH. */
+dg_status dg_partition_plan(const int32_t* tet_vid, const double* tet_xyz, const int8_t* bc_tag, int64_t ne,
+                            int renumber, int k, int r, int64_t* first, int64_t* count, int64_t* nhalo,
+                            int32_t* halo_ids, int32_t* halo_part);
+
+/* Split a mesh into k partitions on its device: one local mesh per partition (own elements, then
+ * the halo, connectivity renumbered), its state buffer with room for the halo, and the exchange
+ * index lists.  Tables are shared with the mesh, which must outlive the partition.  Synchronises
+ * the stream.  Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_partition_create(dg_mesh* mesh, int k, void* stream, dg_partition** out);
+dg_status dg_partition_destroy(dg_partition* part);
+
+/* The plan of partition r (as dg_partition_plan), from a partition object. */
+dg_status dg_partition_info(const dg_partition* part, int r, int64_t* first, int64_t* count, int64_t* nhalo,
+                            int32_t* halo_ids, int32_t* halo_part);
+
+/* Residual through the partitions: U (device FP64, caller order) is split into the partitions'
+ * own blocks, the halos are exchanged, every partition evaluates its own elements' residual on its
+ * local mesh (the same kernel as dg_residual), and R (device FP64, caller order) is assembled.
+ * Every element's residual is computed from the same inputs as by dg_residual, so R is bitwise the
+ * same.  Uses the mesh's work buffers. */
+dg_status dg_partition_residual(dg_partition* part, const double* U, double* R, void* stream);
+
+/* The reductions of a partitioned run at U (device FP64, caller order): every partition's local
+ * time-step minimum and its local totals over its own elements, then the minimum and the sums over
+ * the partitions in partition order (a multi-process run's allreduce(min) and allreduce(sum)).
+ *   dt (host, may be NULL): cfl times the minimum, as dg_stable_dt;
+ *   totals (host [5], may be NULL), kinetic_energy (host, may be NULL): as dg_integrals, equal to
+ *   its values up to the summation order.  Synchronises the stream. */
+dg_status dg_partition_reductions(dg_partition* part, const double* U, double cfl, double* dt, double totals[5],
+                                  double* kinetic_energy, void* stream);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* dg_last_error(void);

@@ -201,6 +201,27 @@ class Problem:
         ke = 0.5 * np.sum(Uq[..., 1:4] ** 2, axis=-1) / Uq[..., 0]
         return np.array(tot), math.fsum((wdet * ke).ravel())
 
+    def boundary_flux(self, U):
+        """Integral of the numerical flux over the boundary faces,
+        B_v = sum_{boundary f} int_f H_v(Q-, Q_b, n) dS (the boundary-face line of
+        Eq. 11 with the constant test function): interior fluxes cancel in pairs,
+        so d/dt int U_v dx = -B_v.  FP64, summed exactly (fsum)."""
+        U = np.asarray(U, dtype=np.float64)
+        parts = [[] for _ in range(5)]
+        for f in range(4):
+            eb = np.nonzero(self.nbr[:, f] < 0)[0]
+            if len(eb) == 0:
+                continue
+            n, area = face_normal_area(self.xyz, eb, f)
+            Um = _es("qj,evj->eqv", self.phi_f[f], U[eb])
+            nn = np.broadcast_to(n[:, None, :], Um.shape[:-1] + (3,))
+            bt = np.broadcast_to(self.btype[eb, f][:, None], Um.shape[:-1])
+            H = self.numflux(Um, self.ghost(Um, nn, bt), nn)
+            contrib = _es("q,e,eqv->ev", self.wf, 2.0 * area, H)
+            for v in range(5):
+                parts[v].extend(contrib[:, v].tolist())
+        return np.array([math.fsum(x) for x in parts])
+
     def kinetic_energy_grad(self, U):
         """d/dU of int |m|^2 / (2 rho) over the mesh (volume rule), [ne,5,nb]."""
         Uq = _es("qj,evj->eqv", self.phi_q, U)

@@ -55,6 +55,7 @@ dg_status upload(T** dst, const T* src, size_t n, cudaStream_t s) {
 void free_mesh(dg_mesh* m) {
     if (!m) return;
     cudaFree(m->d_nbr);
+    cudaFree(m->d_bface);
     cudaFree(m->d_fcode);
     cudaFree(m->d_perm);
     cudaFree(m->d_jinv);
@@ -63,6 +64,7 @@ void free_mesh(dg_mesh* m) {
     cudaFree(m->d_tab64);
     cudaFree(m->d_fperm);
     cudaFree(m->d_tab16);
+    cudaFree(m->d_tabws);
     cudaFree(m->d_mslot);
     cudaFree(m->d_mlist);
     cudaFree(m->d_mhdr);
@@ -162,9 +164,17 @@ dg_status dg_mesh_create(const int32_t* tet_vid, const double* tet_xyz, const in
     DG_TRY(upload(&m->d_perm, m->host.perm.data(), m->host.perm.size(), s));
     DG_TRY(upload(&m->d_jinv64, m->host.jinv.data(), m->host.jinv.size(), s));
     DG_TRY(upload(&m->d_fperm, m->ref.fperm.data(), m->ref.fperm.size(), s));
-    // FP64 tables followed by the volume points' reference coordinates
+    // FP64 tables followed by the volume points' reference coordinates and the face weights
     std::vector<double> tab64 = m->ref.tab;
     tab64.insert(tab64.end(), m->ref.vol_xi.begin(), m->ref.vol_xi.end());
+    tab64.insert(tab64.end(), m->ref.face_w.begin(), m->ref.face_w.end());
+    {
+        std::vector<int32_t> bf;
+        for (int64_t i = 0; i < (int64_t)m->host.nbr.size(); ++i)
+            if (m->host.nbr[i] < 0) bf.push_back((int32_t)i);   // i = 4 e + f
+        if (bf.empty()) bf.push_back(0);                         // never read: n_bfaces is 0
+        DG_TRY(upload(&m->d_bface, bf.data(), bf.size(), s));
+    }
     DG_TRY(upload(&m->d_tab64, tab64.data(), tab64.size(), s));
     std::vector<float> tab32(m->ref.tab.begin(), m->ref.tab.end());
     std::vector<float> jinv32(m->host.jinv.begin(), m->host.jinv.end());
@@ -172,6 +182,9 @@ dg_status dg_mesh_create(const int32_t* tet_vid, const double* tet_xyz, const in
         std::vector<uint16_t> t16;
         dg::build_mixed_tables(m->p, m->precision == DG_MIXED_BF16, m->ref, t16, m->mix_inv_b1, m->mix_inv_b2);
         DG_TRY(upload(&m->d_tab16, t16.data(), t16.size(), s));
+        std::vector<uint16_t> tws;
+        dg::build_ws_tables(m->p, m->precision == DG_MIXED_BF16, m->ref, tws, m->ws_inv_b1, m->ws_inv_b2);
+        DG_TRY(upload(&m->d_tabws, tws.data(), tws.size(), s));
         std::vector<uint32_t> slot;
         std::vector<uint8_t> lists;
         std::vector<int32_t> cnt, xnbr;
@@ -500,6 +513,30 @@ dg_status dg_integrals(dg_mesh* m, const double* U, double totals[5], double* ke
     DG_CUDA(cudaStreamSynchronize(s));
     for (int v = 0; v < 5; ++v) totals[v] = m->h_red[v];
     if (ke) *ke = m->h_red[5];
+    return DG_OK;
+}
+
+dg_status dg_boundary_flux(dg_mesh* m, const double* U, int stage, double out[5], void* stream) {
+    if (!m || !out) return fail(DG_ERR_ARG, "mesh and out must be non-NULL");
+    if (stage < 0 || stage > 2) return fail(DG_ERR_ARG, "stage must be 0, 1 or 2");
+    if (!U && !m->has_state) return fail(DG_ERR_NOSTATE, "no state set and U is NULL");
+    cudaStream_t s = as_stream(stream);
+    const void* in = m->d_B[stage];
+    if (U) {
+        dg_status st = ensure_work_buffers(m);
+        if (st != DG_OK) return st;
+        DG_CUDA(dg::launch_gather(m, U, m->d_W[0], s));
+        in = m->d_W[0];
+    }
+    if (m->host.n_bfaces == 0) {
+        for (int v = 0; v < 5; ++v) out[v] = 0.0;
+        return DG_OK;
+    }
+    double* d_out = m->d_red + RED_SLOTS;
+    DG_CUDA(dg::launch_boundary_flux(m, in, m->d_red, d_out, s));
+    DG_CUDA(cudaMemcpyAsync(m->h_red, d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    for (int v = 0; v < 5; ++v) out[v] = m->h_red[v];
     return DG_OK;
 }
 

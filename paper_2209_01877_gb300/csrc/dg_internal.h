@@ -56,6 +56,7 @@ struct dg_mesh {
     dg::RefData ref;
     // device buffers
     int32_t* d_nbr = nullptr;
+    int32_t* d_bface = nullptr;    // boundary (element, face) codes 4 e + f, ascending (internal order)
     uint8_t* d_fcode = nullptr;
     int32_t* d_perm = nullptr;     // internal -> caller
     void* d_jinv = nullptr;        // Real [ne][9]
@@ -65,6 +66,8 @@ struct dg_mesh {
     int8_t* d_fperm = nullptr;
     uint16_t* d_tab16 = nullptr;   // f16 operand images of the tables (mixed precision)
     float mix_inv_b1 = 1.f, mix_inv_b2 = 1.f;
+    uint16_t* d_tabws = nullptr;   // table images of the warp-specialised stage kernel
+    float ws_inv_b1 = 1.f, ws_inv_b2 = 1.f;
     // mixed precision: per tile of consecutive elements, the slot codes, the cross and work
     // lists and the tile headers (build_mixed_tiles)
     uint32_t* d_mslot = nullptr;
@@ -101,6 +104,7 @@ cudaError_t launch_scatter(dg_mesh* m, const void* internal, double* user, cudaS
 cudaError_t launch_scatter_f32(dg_mesh* m, const float* internal, double* user, cudaStream_t s);
 cudaError_t launch_stable_dt(dg_mesh* m, const void* U, double* d_out, cudaStream_t s);
 cudaError_t launch_integrals(dg_mesh* m, const void* U, double* d_out6, cudaStream_t s);
+cudaError_t launch_boundary_flux(dg_mesh* m, const void* U, double* d_partial, double* d_out5, cudaStream_t s);
 cudaError_t launch_project(dg_mesh* m, const double* f, double* U, cudaStream_t s);
 cudaError_t launch_volume_points(dg_mesh* m, const double* d_x0J, double* xyz, cudaStream_t s);
 cudaError_t launch_residual_vjp(dg_mesh* m, const void* U, const void* lam, const void* X, const void* Y,
@@ -112,6 +116,10 @@ cudaError_t launch_residual_mixed(dg_mesh* m, const float* U_hi, const float* U_
                                   double b, cudaStream_t s);
 void build_mixed_tables(int p, bool bf16, const RefData& ref, std::vector<uint16_t>& out, float& inv_b1,
                         float& inv_b2);
+void build_ws_tables(int p, bool bf16, const RefData& ref, std::vector<uint16_t>& out, float& inv_b1,
+                     float& inv_b2);
+cudaError_t launch_stage_ws(dg_mesh* m, const float* U_hi, const float* U_lo, const float* U0_hi, const float* U0_lo,
+                            float* out_hi, float* out_lo, int mode, double dt, double a, double b, cudaStream_t s);
 void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vector<uint8_t>& lists,
                        std::vector<int32_t>& hdr, std::vector<int32_t>& xnbr);
 dg_status set_error(dg_status code, const char* msg);   // sets dg_last_error() for the calling thread

@@ -27,6 +27,8 @@ EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_element_ord
             "dg_volume_points", "dg_project", "dg_set_state", "dg_get_state", "dg_residual", "dg_ns_residual",
             "dg_rk_stage", "dg_rk3_step", "dg_stable_dt", "dg_integrals", "dg_residual_vjp", "dg_rk3_step_vjp",
             "dg_kinetic_energy_grad", "dg_sync_status", "dg_reference_data", "dg_conserved_totals_noalloc",
+            "dg_boundary_flux", "dg_partition_plan", "dg_partition_create", "dg_partition_destroy",
+            "dg_partition_info", "dg_partition_residual", "dg_partition_reductions",
             "dg_last_error"]
 
 
@@ -70,6 +72,15 @@ def load():
             "dg_rk3_step": [vp, C.c_double, C.c_int, vp],
             "dg_stable_dt": [vp, C.c_double, C.POINTER(C.c_double), vp],
             "dg_integrals": [vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double), vp],
+            "dg_boundary_flux": [vp, vp, C.c_int, C.POINTER(C.c_double), vp],
+            "dg_partition_plan": [vp, vp, vp, i64, C.c_int, C.c_int, C.c_int, C.POINTER(i64), C.POINTER(i64),
+                                  C.POINTER(i64), vp, vp],
+            "dg_partition_create": [vp, C.c_int, vp, C.POINTER(vp)],
+            "dg_partition_destroy": [vp],
+            "dg_partition_info": [vp, C.c_int, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), vp, vp],
+            "dg_partition_residual": [vp, vp, vp, vp],
+            "dg_partition_reductions": [vp, vp, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double), vp],
             "dg_residual_vjp": [vp, vp, vp, vp, vp],
             "dg_rk3_step_vjp": [vp, vp, C.c_double, vp, vp, vp],
             "dg_kinetic_energy_grad": [vp, vp, vp, vp],
@@ -240,6 +251,14 @@ def dg_integrals(mesh, U=None, stream=None):
     return np.array(list(tot)), ke.value
 
 
+def dg_boundary_flux(mesh, U=None, stage=0, stream=None):
+    """Boundary-flux integral (5 values): of U (device, caller order), or with U None of the
+    internal state (stage 0) or of the intermediate RK state U1 / U2 (stage 1 / 2)."""
+    out = (C.c_double * 5)()
+    _check(load().dg_boundary_flux(mesh, _dptr(U), int(stage), out, _stream(stream)))
+    return np.array(list(out))
+
+
 def dg_residual_vjp(mesh, U, lam, out, stream=None):
     _check(load().dg_residual_vjp(mesh, _dptr(U), _dptr(lam), _dptr(out), _stream(stream)))
 
@@ -286,6 +305,59 @@ def dg_conserved_totals_noalloc(U, detJ, totals, stream=None, ne=None):
         raise ValueError(f"ne={n} exceeds U ({U.shape[0]} elements) or detJ ({detJ.numel()} values)")
     _check(load().dg_conserved_totals_noalloc(_dptr(U), _dptr(detJ), n, int(U.shape[2]), _dptr(totals),
                                               _stream(stream)))
+
+
+def dg_partition_plan(tet_vid, tet_xyz, bc_tag, renumber, k, r):
+    """Host only: (first, count, halo_ids, halo_part) of partition r of k."""
+    vid, pv = _hptr(tet_vid, np.int32)
+    xyz, px = _hptr(tet_xyz, np.float64)
+    ne = vid.shape[0]
+    pb = None
+    if bc_tag is not None:
+        tag, pb = _hptr(bc_tag, np.int8)
+    first, count, nh = C.c_int64(), C.c_int64(), C.c_int64()
+    lib = load()
+    _check(lib.dg_partition_plan(pv, px, pb, ne, int(renumber), int(k), int(r), C.byref(first), C.byref(count),
+                                 C.byref(nh), None, None))
+    ids = np.empty(nh.value, dtype=np.int32)
+    part = np.empty(nh.value, dtype=np.int32)
+    _check(lib.dg_partition_plan(pv, px, pb, ne, int(renumber), int(k), int(r), None, None, None,
+                                 C.c_void_p(ids.ctypes.data), C.c_void_p(part.ctypes.data)))
+    return first.value, count.value, ids, part
+
+
+def dg_partition_create(mesh, k, stream=None):
+    out = C.c_void_p()
+    _check(load().dg_partition_create(mesh, int(k), _stream(stream), C.byref(out)))
+    return out
+
+
+def dg_partition_destroy(part):
+    _check(load().dg_partition_destroy(part))
+
+
+def dg_partition_info(part, r):
+    first, count, nh = C.c_int64(), C.c_int64(), C.c_int64()
+    lib = load()
+    _check(lib.dg_partition_info(part, int(r), C.byref(first), C.byref(count), C.byref(nh), None, None))
+    ids = np.empty(nh.value, dtype=np.int32)
+    pp = np.empty(nh.value, dtype=np.int32)
+    _check(lib.dg_partition_info(part, int(r), None, None, None, C.c_void_p(ids.ctypes.data),
+                                 C.c_void_p(pp.ctypes.data)))
+    return first.value, count.value, ids, pp
+
+
+def dg_partition_residual(part, U, R, stream=None):
+    _check(load().dg_partition_residual(part, _dptr(U), _dptr(R), _stream(stream)))
+
+
+def dg_partition_reductions(part, U, cfl, stream=None):
+    """(dt, totals[5], kinetic energy) reduced over the partitions."""
+    dt, ke = C.c_double(), C.c_double()
+    tot = (C.c_double * 5)()
+    _check(load().dg_partition_reductions(part, _dptr(U), float(cfl), C.byref(dt), tot, C.byref(ke),
+                                          _stream(stream)))
+    return dt.value, np.array(list(tot)), ke.value
 
 
 def dg_last_error():

@@ -19,9 +19,11 @@ import make_golden as G  # noqa: E402
 
 @pytest.mark.parametrize("case", sorted(G.CASES))
 def test_oracle_reproduces_fixture(case):
+    """To 1e-12 of the largest entry, the FP64 parity bar: numpy builds with other
+    summation orders (e.g. on an Arm host) move the residual by ~2e-13 of it."""
     _, R = G.compute(case)
     stored = G.read(case).reshape(R.shape)
-    np.testing.assert_allclose(R, stored, rtol=0, atol=1e-13 * np.abs(stored).max())
+    np.testing.assert_allclose(R, stored, rtol=0, atol=1e-12 * np.abs(stored).max())
 
 
 @pytest.mark.gpu

@@ -33,7 +33,6 @@ from gpu_helpers import (gpu_residual, make_mesh, max_rel_err, residual_term_sca
 pytestmark = pytest.mark.gpu
 TOL64 = 1e-12
 TOL32 = 1e-4
-PLAIN_BOX = 1e-10
 
 
 def _box(nx=4, ny=3, nz=3):
@@ -75,9 +74,10 @@ def test_residual_periodic_fp64(p, flux):
 @pytest.mark.parametrize("p", [1, 2, 3])
 @pytest.mark.parametrize("flux", ["rusanov", "roe"])
 def test_residual_box_boundaries_fp64(p, flux):
-    """A pulse in a channel: away from the pulse the residual is free-stream
-    cancellation, so the term-scale floor is what the 1e-12 bar rests on; the
-    plain error is held to PLAIN_BOX (measured on GB300, with margin)."""
+    """A pulse in a channel with walls and far-field faces.  On this small box
+    the plain bar holds as well (measured on GB300: at most 4e-14); on the
+    full-size channel, where most elements see free stream only, the
+    term-scale floor is what the 1e-12 bar rests on."""
     m = _box()
     Uinf = I.freestream_state(0.3)
     P = Problem(m.tet_vid, m.tet_xyz, m.bc_tag, p=p, flux=flux, freestream=Uinf)
@@ -88,7 +88,7 @@ def test_residual_box_boundaries_fp64(p, flux):
     plain, floored = _both_bars(gpu_residual(M, U), R, P, U)
     print(f"box p={p} {flux}: plain {plain:.2e}, term-scaled {floored:.2e}")
     assert floored < TOL64
-    assert plain < PLAIN_BOX
+    assert plain < TOL64
 
 
 @pytest.mark.parametrize("p", [1, 3])

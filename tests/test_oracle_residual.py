@@ -112,6 +112,62 @@ def test_design_order_isentropic_vortex(p, levels):
     assert order > p + 1 - 0.3, (errs, order)
 
 
+def _box_pulse(flux, p=2):
+    m = I.make_box_channel(4, 2, 2, jitter=0.15)
+    Uinf = I.freestream_state(0.3)
+    P = Problem(m.tet_vid, m.tet_xyz, m.bc_tag, p=p, flux=flux, freestream=Uinf)
+
+    def field(x):
+        U = I.gaussian_pulse(x, (1.7, 0.5, 0.5), width=0.3)
+        U[..., 2] += 0.05 * U[..., 0]
+        return U
+    return m, P, P.project(field)
+
+
+@pytest.mark.parametrize("flux", ["rusanov", "roe"])
+def test_boundary_flux_balances_the_totals(flux):
+    """d/dt int U dx = -(boundary flux integral): interior face fluxes cancel in
+    pairs, so the rate of the totals from the residual (mode 0) is minus the
+    boundary integral of Eq. 11's boundary-face line."""
+    m, P, U = _box_pulse(flux)
+    R = P.residual(U)
+    rate = np.einsum("e,ev->v", P.det, R[:, :, 0]) * math.sqrt(6.0) / 6.0
+    B = P.boundary_flux(U)
+    scale = np.einsum("e,ev->v", P.det, np.abs(R[:, :, 0])) * math.sqrt(6.0) / 6.0
+    # per conserved quantity (mass, momentum as one vector quantity, energy)
+    for group in ((0,), (1, 2, 3), (4,)):
+        g = list(group)
+        assert np.abs(rate[g] + B[g]).max() < 1e-13 * (scale[g].max() + np.abs(B[g]).max()), (rate, B)
+    assert np.abs(B).max() > 1e-3
+
+
+@pytest.mark.parametrize("flux", ["rusanov", "roe"])
+def test_boundary_flux_closed_form_wall_inflow(flux):
+    """Uniform free stream (rho = p = 1, u = 0.3 c along +x) in the channel with
+    the inflow side x = 0 turned into a slip wall: the far-field outflow side
+    passes F(U).n = (rho u, rho u^2 + p, 0, 0, (E + p) u) through its unit area,
+    the x = 0 wall returns -(rho u^2 + p) + rho u s (Rusanov: s = |u| + c; Roe:
+    s = the Roe-averaged sound speed of the state and its reflection, whose
+    average velocity is 0 and enthalpy H = c^2/(gamma-1) + u^2/2, so
+    s^2 = c^2 + (gamma-1) u^2/2) and nothing else, and the y, z walls cancel
+    pairwise, so B = (rho u, rho u s, 0, 0, (E + p) u)."""
+    m = I.make_box_channel(4, 2, 2, jitter=0.15)
+    tag = m.bc_tag.copy()
+    for f in range(4):
+        others = [k for k in range(4) if k != f]
+        on_x0 = np.all(m.tet_xyz[:, others, 0] == 0.0, axis=1)
+        tag[on_x0, f] = 1
+    Uinf = I.freestream_state(0.3)
+    P = Problem(m.tet_vid, m.tet_xyz, tag, p=2, flux=flux, freestream=Uinf)
+    U = P.project(lambda x: np.broadcast_to(Uinf, x.shape[:-1] + (5,)).copy())
+    rho, u, p, g = 1.0, 0.3 * math.sqrt(1.4), 1.0, 1.4
+    c = math.sqrt(g * p / rho)
+    E = p / (g - 1) + 0.5 * rho * u * u
+    s = abs(u) + c if flux == "rusanov" else math.sqrt(c * c + 0.5 * (g - 1) * u * u)
+    ref = np.array([rho * u, rho * u * s, 0.0, 0.0, (E + p) * u])
+    np.testing.assert_allclose(P.boundary_flux(U), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
 class _Linear:
     def __init__(self, lam):
         self.lam = lam
