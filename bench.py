@@ -664,18 +664,25 @@ def run_study(args):
             dg.dg_rk_stage(M.handle, st, dt)
         torch.cuda.synchronize()
         res = {}
-        for name in ("dg_rk3_step", "dg_rk_stage x 3"):
+        for name in ("dg_rk3_step", "dg_rk_stage x 3", "dg_rk3_step, new dt every call"):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
             a.record()
             if name == "dg_rk3_step":
                 dg.dg_rk3_step(M.handle, dt, n)
-            else:
+            elif name == "dg_rk_stage x 3":
                 for _ in range(n):
                     for st in (1, 2, 3):
                         dg.dg_rk_stage(M.handle, st, dt)
+            else:
+                # a loop that recomputes dt before every call: 8 steps per call, the captured graph
+                # updated in place for each new dt
+                for i in range(n // 8):
+                    dg.dg_rk3_step(M.handle, dt * (1.0 - 1e-3 * (i % 7)), 8)
             b.record()
             torch.cuda.synchronize()
             res[name] = a.elapsed_time(b) * 1e3 / n
+            res[name + " (host wall)"] = (time.perf_counter() - t0) * 1e6 / n
         dg.dg_sync_status(M.handle)
         M.close()
         out.update({"steps": n, "tets": mesh.ne, "us_per_step": res,

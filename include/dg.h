@@ -255,8 +255,8 @@ dg_status dg_conserved_totals_noalloc(const double* U, const double* detJ, int64
 /* ---- Element partitions (the layout of a multi-process run) ------------------------------------
  * The paper renumbers its grid once before time stepping, for every process (Sec. III-B).  A
  * partitioned run gives partition r a contiguous slab of the renumbered element order (RCM, Morton
- * or Hilbert keep slabs spatially compact), slab boundaries on multiples of 12 elements (the tile of
- * the mixed-precision kernel), and a halo: the ascending list of other partitions' elements that its
+ * or Hilbert keep slabs spatially compact), slab boundaries on multiples of 96 elements (a common
+ * multiple of the kernels' tile sizes, so every partition's tiles are the whole mesh's), and a halo: the ascending list of other partitions' elements that its
  * own elements' faces reach.  One residual evaluation needs one halo exchange; the time-step minimum
  * and the conserved totals are reduced over the partitions.  Here the k partitions live on the
  * mesh's device: the exchange is a device gather from the owning partitions' state buffers into each
@@ -270,7 +270,7 @@ typedef struct dg_partition dg_partition;   /* opaque; owns its local meshes' de
  *   nhalo: the halo size; halo_ids [nhalo] (ascending internal ids) and halo_part [nhalo] (the
  *   owning partition of each), both host, caller-sized, may be NULL (call first with NULL to get
  *   nhalo).  Any output may be NULL.
- * Errors: DG_ERR_ARG (bad sizes, r outside [0, k), k too large for a 12-element tile per slab),
+ * Errors: DG_ERR_ARG (bad sizes, r outside [0, k), k too large for 96 elements per slab),
  * DG_ERR_MESH. */
 dg_status dg_partition_plan(const int32_t* tet_vid, const double* tet_xyz, const int8_t* bc_tag, int64_t ne,
                             int renumber, int k, int r, int64_t* first, int64_t* count, int64_t* nhalo,

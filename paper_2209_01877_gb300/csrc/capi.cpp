@@ -64,7 +64,6 @@ void free_mesh(dg_mesh* m) {
     cudaFree(m->d_tab64);
     cudaFree(m->d_fperm);
     cudaFree(m->d_tab16);
-    cudaFree(m->d_tabws);
     cudaFree(m->d_mslot);
     cudaFree(m->d_mlist);
     cudaFree(m->d_mhdr);
@@ -182,9 +181,6 @@ dg_status dg_mesh_create(const int32_t* tet_vid, const double* tet_xyz, const in
         std::vector<uint16_t> t16;
         dg::build_mixed_tables(m->p, m->precision == DG_MIXED_BF16, m->ref, t16, m->mix_inv_b1, m->mix_inv_b2);
         DG_TRY(upload(&m->d_tab16, t16.data(), t16.size(), s));
-        std::vector<uint16_t> tws;
-        dg::build_ws_tables(m->p, m->precision == DG_MIXED_BF16, m->ref, tws, m->ws_inv_b1, m->ws_inv_b2);
-        DG_TRY(upload(&m->d_tabws, tws.data(), tws.size(), s));
         std::vector<uint32_t> slot;
         std::vector<uint8_t> lists;
         std::vector<int32_t> cnt, xnbr;

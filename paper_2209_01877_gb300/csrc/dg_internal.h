@@ -66,8 +66,6 @@ struct dg_mesh {
     int8_t* d_fperm = nullptr;
     uint16_t* d_tab16 = nullptr;   // f16 operand images of the tables (mixed precision)
     float mix_inv_b1 = 1.f, mix_inv_b2 = 1.f;
-    uint16_t* d_tabws = nullptr;   // table images of the warp-specialised stage kernel
-    float ws_inv_b1 = 1.f, ws_inv_b2 = 1.f;
     // mixed precision: per tile of consecutive elements, the slot codes, the cross and work
     // lists and the tile headers (build_mixed_tiles)
     uint32_t* d_mslot = nullptr;
@@ -116,10 +114,6 @@ cudaError_t launch_residual_mixed(dg_mesh* m, const float* U_hi, const float* U_
                                   double b, cudaStream_t s);
 void build_mixed_tables(int p, bool bf16, const RefData& ref, std::vector<uint16_t>& out, float& inv_b1,
                         float& inv_b2);
-void build_ws_tables(int p, bool bf16, const RefData& ref, std::vector<uint16_t>& out, float& inv_b1,
-                     float& inv_b2);
-cudaError_t launch_stage_ws(dg_mesh* m, const float* U_hi, const float* U_lo, const float* U0_hi, const float* U0_lo,
-                            float* out_hi, float* out_lo, int mode, double dt, double a, double b, cudaStream_t s);
 void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vector<uint8_t>& lists,
                        std::vector<int32_t>& hdr, std::vector<int32_t>& xnbr);
 dg_status set_error(dg_status code, const char* msg);   // sets dg_last_error() for the calling thread

@@ -51,7 +51,6 @@
 // status bit and leaves its tile loop (all its threads together); the CTA
 // frees its tensor memory when both contexts are done.
 #include <algorithm>
-#include <cstdlib>
 #include <cstring>
 
 #include <cuda_bf16.h>
@@ -107,9 +106,13 @@ struct SPlan {
     static constexpr int N2 = r8(NB);
     // f16 table images in global memory (halves): T1 a|b, T2 a|b
     static constexpr int G_T1 = 0, G_T2 = 2 * N1 * K1, TAB_HALVES = G_T2 + 2 * N2 * K2;
-    // tensor memory of a context: D1 (own points), D2 (projection: hi-table and lo-table products)
+    // tensor memory of a context: D1 (own points), then NCH accumulators of the projection, each
+    // holding hi-table and lo-table products (2 N2 columns): the K steps of MMA 2 go round-robin
+    // over independent accumulators, so consecutive MMAs do not wait on one another
+    static constexpr int NCH = 3;
     static constexpr int C_D1 = 0, C_D2 = r16(N1);
-    static_assert(C_D2 + 2 * N2 <= CTX_COLS, "tensor memory");
+    static_assert(C_D2 + NCH * 2 * N2 <= CTX_COLS, "tensor memory");
+    static_assert(K2 / 16 >= NCH, "every accumulator receives a K step");
     // point-state staging [ET][5][VSTR]: VSTR = 8 (mod 32) and >= the staged columns, so USTR =
     // 5 VSTR = 8 (mod 32) too; then row 5e + v starts at bank 8 (e + v) (mod 32), any 4
     // consecutive rows start 8 banks apart (conflict-free 8-byte staging stores of a half warp),
@@ -138,7 +141,7 @@ struct SPlan {
     static constexpr int X_CODE = a128(X_EL + ET * ELW * 4);              // uint32 [SLOTS]
     static constexpr int X_LIST = X_CODE + SLOTS * 4;                      // uint8 [2*SLOTS]: cross, work
     static constexpr int X_C = a128(X_LIST + 2 * SLOTS);                   // float [SLOTS][5 Nb] neighbour blocks
-    static constexpr int X_MB = a128(X_C + SZ_C);                          // mbarrier
+    static constexpr int X_MB = a128(X_C + SZ_C);                          // mbarrier, then the drain mbarrier
     static constexpr int CTX_BYTES = a128(X_MB + 16);
     static constexpr int O_PERM = O_CTX + 2 * CTX_BYTES;                   // int8 [6][NQF]
     static constexpr int O_SLOT = a128(O_PERM + 6 * NQF);                  // tmem slot
@@ -264,7 +267,10 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         }
     }
     __syncthreads();
-    if (ct == 0) tc::mbar_init(mbar);
+    if (ct == 0) {
+        tc::mbar_init(mbar);
+        tc::mbar_init(mbar + 1);   // drain: one commit after the last MMA of the context
+    }
     if (warp == 0) tc::tmem_alloc(tslot, TMEM_COLS);
     tc::fence_async_smem();
     tc::fence_before();
@@ -350,7 +356,11 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
             const int fn = (sCode[sList[c]] >> 19) & 3;
             const float* ph = sPhiF + (fn * NQF + p) * NB;
             const float* cf = sC + c * NV5;
-            float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            // sum_j c_vj phi_j as packed pairs of modes (j, j + 1) (NB is even for every order): partial
+            // sums of the even and the odd modes, added at the end
+            float2 acc[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) acc[v] = f2(0.f);
             if constexpr (NB % 4 == 0) {
                 // rows of NB floats start on 16-byte boundaries: 4 modes per shared load
 #pragma unroll
@@ -359,20 +369,21 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
 #pragma unroll
                     for (int v = 0; v < 5; ++v) {
                         const float4 x = *reinterpret_cast<const float4*>(cf + v * NB + j);
-                        acc[v] = fmaf(x.x, w.x, fmaf(x.y, w.y, fmaf(x.z, w.z, fmaf(x.w, w.w, acc[v]))));
+                        acc[v] = fma2(make_float2(x.x, x.y), make_float2(w.x, w.y), acc[v]);
+                        acc[v] = fma2(make_float2(x.z, x.w), make_float2(w.z, w.w), acc[v]);
                     }
                 }
             } else {
 #pragma unroll
-                for (int j = 0; j < NB; ++j) {
-                    const float w = ph[j];
+                for (int j = 0; j < NB; j += 2) {
+                    const float2 w = *reinterpret_cast<const float2*>(ph + j);
 #pragma unroll
-                    for (int v = 0; v < 5; ++v) acc[v] = fmaf(cf[v * NB + j], w, acc[v]);
+                    for (int v = 0; v < 5; ++v) acc[v] = fma2(*reinterpret_cast<const float2*>(cf + v * NB + j), w, acc[v]);
                 }
             }
             float* nd = sN + c * 5 * NQF4 + p;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) nd[v * NQF4] = acc[v];
+            for (int v = 0; v < 5; ++v) nd[v * NQF4] = acc[v].x + acc[v].y;
         }
         // per element while the tensor cores work (used by the faces below and the flux phase)
         if (ct >= 64 && ct < 64 + ET) {
@@ -536,14 +547,15 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         // ---- MMA 2: projection onto the weighted basis gradients + face lift ----------------------
         // T2b follows T2a in shared memory in the same K-major layout, so [T2a; T2b] is one operand
         // of 2 N2 rows: one MMA per K step writes the hi-table products to columns [0, N2) and the
-        // lo-table products to [N2, 2 N2); the epilogue adds the two
+        // lo-table products to [N2, 2 N2) of accumulator ks % NCH; the epilogue adds them all
         if (ct == 0) {
             constexpr uint64_t KSTEP = 16;
             const uint32_t id2 = tc::idesc_f16(64, 2 * N2, BF);
             const uint64_t dA2 = tc::kdesc(sA2, 0, K2), dT2 = tc::kdesc(sT2a, 0, K2);
 #pragma unroll
             for (int ks = 0; ks < K2 / 16; ++ks)
-                tc::mma(tmem + S::C_D2, dA2 + KSTEP * ks, dT2 + KSTEP * ks, id2, ks != 0);
+                tc::mma(tmem + S::C_D2 + (ks % S::NCH) * 2 * N2, dA2 + KSTEP * ks, dT2 + KSTEP * ks, id2,
+                        ks >= S::NCH);
             tc::commit(mbar);
         }
         // the next tile's neighbour blocks (sC is free: this tile's traces are done)
@@ -592,22 +604,29 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         tc::fence_after();
         // ---- epilogue: residual, or the RK stage in float-float -----------------------------------
         {
-            float d[2][3];   // R at (row A | B) x (pair 0, pair 1, single)
+            static_assert(S::NCH == 3, "the epilogue loads three accumulators");
+            float2 dp[2];    // R at (row A | B) x the mode pair
+            float ds[2];     // R at (row A | B) x the single mode
             {
-                float x0[4], x1[4];
-                ld16x256x2(tmem + lane_base + S::C_D2 + 8 * part, tmem + lane_base + S::C_D2 + N2 + 8 * part, x0, x1);
-                d[0][0] = x0[0] + x1[0];
-                d[0][1] = x0[1] + x1[1];
-                d[1][0] = x0[2] + x1[2];
-                d[1][1] = x0[3] + x1[3];
-                d[0][2] = d[1][2] = 0.f;
+                const uint32_t base = tmem + lane_base + S::C_D2 + 8 * part;
+                const uint32_t t[6] = {base, base + N2, base + 2 * N2, base + 3 * N2, base + 4 * N2, base + 5 * N2};
+                float x[6][4];
+                ld16x256x6(t, x);
+                dp[0] = make_float2(((x[0][0] + x[1][0]) + (x[2][0] + x[3][0])) + (x[4][0] + x[5][0]),
+                                    ((x[0][1] + x[1][1]) + (x[2][1] + x[3][1])) + (x[4][1] + x[5][1]));
+                dp[1] = make_float2(((x[0][2] + x[1][2]) + (x[2][2] + x[3][2])) + (x[4][2] + x[5][2]),
+                                    ((x[0][3] + x[1][3]) + (x[2][3] + x[3][3])) + (x[4][3] + x[5][3]));
+                ds[0] = ds[1] = 0.f;
             }
             if (part == 1 && N2 > 16) {
-                float y0[2], y1[2];
-                ld16x128x2(tmem + lane_base + S::C_D2 + 16, tmem + lane_base + S::C_D2 + N2 + 16, y0, y1);
-                d[0][2] = y0[0] + y1[0];
-                d[1][2] = y0[1] + y1[1];
+                const uint32_t base = tmem + lane_base + S::C_D2 + 16;
+                const uint32_t t[6] = {base, base + N2, base + 2 * N2, base + 3 * N2, base + 4 * N2, base + 5 * N2};
+                float y[6][2];
+                ld16x128x6(t, y);
+                ds[0] = ((y[0][0] + y[1][0]) + (y[2][0] + y[3][0])) + (y[4][0] + y[5][0]);
+                ds[1] = ((y[0][1] + y[1][1]) + (y[2][1] + y[3][1])) + (y[4][1] + y[5][1]);
             }
+            const float ca = a.a, cbdt = a.bdt;
 #pragma unroll
             for (int rr = 0; rr < 2; ++rr) {
                 const bool ok = rr == 0 ? okA : okB;
@@ -615,32 +634,35 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 const int r = rr == 0 ? rA : rB;
                 const int64_t g = rr == 0 ? gA : gB;
                 const float inv = sEl[(r / 5) * ELW + 49];
-                float oh[3], ol[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float R = d[rr][c] * inv;
-                    if (a.mode == 0) {
-                        oh[c] = R;
-                        ol[c] = 0.f;
-                    } else {
-                        // out = U + a (U0 - U) + b dt R: increment in FP32, float-float sum with U
-                        const float uh = u[rr][0][c], ul = u[rr][1][c];
-                        const float dlt = fmaf(a.a, (u[rr][2][c] - uh) + (u[rr][3][c] - ul), a.bdt * R);
-                        const float sm = uh + dlt;
-                        const float bb = sm - uh;
-                        float err = (uh - (sm - bb)) + (dlt - bb);
-                        err += ul;
-                        oh[c] = sm + err;
-                        ol[c] = err - (oh[c] - sm);
-                    }
+                const float2 R = mul2(dp[rr], f2(inv));
+                const float Rs = ds[rr] * inv;
+                if (a.mode == 0) {
+                    if (pair_in) *reinterpret_cast<float2*>(a.out_hi + g + j0) = R;
+                    if (one_in) a.out_hi[g + j1] = Rs;
+                    continue;
                 }
+                // out = U + a (U0 - U) + b dt R: increment in FP32, float-float sum with U; the mode
+                // pair in packed f32x2 arithmetic (the same operations as the single mode below)
                 if (pair_in) {
-                    *reinterpret_cast<float2*>(a.out_hi + g + j0) = make_float2(oh[0], oh[1]);
-                    if (a.mode != 0) *reinterpret_cast<float2*>(a.out_lo + g + j0) = make_float2(ol[0], ol[1]);
+                    const float2 uh = make_float2(u[rr][0][0], u[rr][0][1]), ul = make_float2(u[rr][1][0], u[rr][1][1]);
+                    const float2 u0h = make_float2(u[rr][2][0], u[rr][2][1]), u0l = make_float2(u[rr][3][0], u[rr][3][1]);
+                    const float2 dlt = fma2(f2(ca), add2(sub2(u0h, uh), sub2(u0l, ul)), mul2(f2(cbdt), R));
+                    const float2 sm = add2(uh, dlt);
+                    const float2 bb = sub2(sm, uh);
+                    const float2 err = add2(add2(sub2(uh, sub2(sm, bb)), sub2(dlt, bb)), ul);
+                    const float2 oh = add2(sm, err);
+                    *reinterpret_cast<float2*>(a.out_hi + g + j0) = oh;
+                    *reinterpret_cast<float2*>(a.out_lo + g + j0) = sub2(err, sub2(oh, sm));
                 }
                 if (one_in) {
-                    a.out_hi[g + j1] = oh[2];
-                    if (a.mode != 0) a.out_lo[g + j1] = ol[2];
+                    const float uh = u[rr][0][2], ul = u[rr][1][2];
+                    const float dlt = fmaf(ca, (u[rr][2][2] - uh) + (u[rr][3][2] - ul), cbdt * Rs);
+                    const float sm = uh + dlt;
+                    const float bb = sm - uh;
+                    const float err = ((uh - (sm - bb)) + (dlt - bb)) + ul;
+                    const float oh = sm + err;
+                    a.out_hi[g + j1] = oh;
+                    a.out_lo[g + j1] = err - (oh - sm);
                 }
             }
         }
@@ -648,7 +670,14 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         ctx_sync(bar_id);
         tc::fence_after();
     }
+    if (ct == 0) tc::commit(mbar + 1);
     tc::cp_async_wait_all();   // no copy outlives the context (a timed-out loop may leave one)
+    // no MMA may still be writing tensor memory when it is freed: after a completion wait gave
+    // up, the MMA it waited for may still be running and its commit still due.  The context's
+    // issuing thread commits once more -- the arrival comes once every MMA it issued has
+    // completed -- and waits for it (bounded: if even that wait gives up, the status bit is set
+    // and the memory is freed regardless)
+    if (ct == 0 && !tc::mbar_wait(mbar + 1, 0, WAIT_ITERS)) atomicOr(a.status, 2u);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -821,8 +850,6 @@ void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vect
 cudaError_t launch_residual_mixed(dg_mesh* m, const float* U_hi, const float* U_lo, const float* U0_hi,
                                   const float* U0_lo, float* out_hi, float* out_lo, int mode, double dt, double ca,
                                   double cb, cudaStream_t s) {
-    if (!std::getenv("DG_OLD_STAGE"))
-        return launch_stage_ws(m, U_hi, U_lo, U0_hi, U0_lo, out_hi, out_lo, mode, dt, ca, cb, s);
     StageArgs r;
     r.U_hi = U_hi;
     r.U_lo = U_lo;

@@ -291,6 +291,55 @@ __device__ __forceinline__ void ld16x128x2(uint32_t t0, uint32_t t1, float a[2],
     b[1] = __uint_as_float(r[3]);
 }
 
+// the same 8 (4) columns of six accumulators, one wait: out[i] from address t[i]
+__device__ __forceinline__ void ld16x256x6(const uint32_t t[6], float out[6][4]) {
+    uint32_t r[24];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%24];\n"
+        "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%4,%5,%6,%7}, [%25];\n"
+        "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%8,%9,%10,%11}, [%26];\n"
+        "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%12,%13,%14,%15}, [%27];\n"
+        "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%16,%17,%18,%19}, [%28];\n"
+        "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%20,%21,%22,%23}, [%29];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+        : "r"(t[0]), "r"(t[1]), "r"(t[2]), "r"(t[3]), "r"(t[4]), "r"(t[5])
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[i][j] = __uint_as_float(r[4 * i + j]);
+}
+__device__ __forceinline__ void ld16x128x6(const uint32_t t[6], float out[6][2]) {
+    uint32_t r[12];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x128b.x1.b32 {%0,%1}, [%12];\n"
+        "tcgen05.ld.sync.aligned.16x128b.x1.b32 {%2,%3}, [%13];\n"
+        "tcgen05.ld.sync.aligned.16x128b.x1.b32 {%4,%5}, [%14];\n"
+        "tcgen05.ld.sync.aligned.16x128b.x1.b32 {%6,%7}, [%15];\n"
+        "tcgen05.ld.sync.aligned.16x128b.x1.b32 {%8,%9}, [%16];\n"
+        "tcgen05.ld.sync.aligned.16x128b.x1.b32 {%10,%11}, [%17];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11])
+        : "r"(t[0]), "r"(t[1]), "r"(t[2]), "r"(t[3]), "r"(t[4]), "r"(t[5])
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        out[i][0] = __uint_as_float(r[2 * i]);
+        out[i][1] = __uint_as_float(r[2 * i + 1]);
+    }
+}
+
+// packed FP32 pairs (sm_100 f32x2 arithmetic)
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 // L2 prefetch of a contiguous range; skipped unless the address is 16-byte aligned (the size
 // is rounded down to a multiple of 16 bytes)
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {

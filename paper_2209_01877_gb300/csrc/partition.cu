@@ -4,8 +4,9 @@
 // is the layout such a run uses:
 //   * partition r owns a contiguous slab [first_r, first_r + count_r) of the internal element
 //     order (RCM, Morton or Hilbert: slabs of a space-filling-curve or RCM order are spatially
-//     compact), slab boundaries on multiples of the 12-element tile of the mixed-precision
-//     kernel, so its tiles are the whole mesh's tiles;
+//     compact), slab boundaries on multiples of 96 elements, a common multiple of every
+//     kernel's tile (12 elements for the mixed-precision kernel; 8, 16 and 32 for the FP64 / FP32
+//     kernel at P3, P2, P1), so a partition's tiles are the whole mesh's tiles;
 //   * its halo is the ascending list of elements of other partitions that its own elements'
 //     faces reach; a local mesh numbers the own elements 0..count-1 and the halo after them,
 //     with the connectivity renumbered accordingly (face codes and boundary tags unchanged);
@@ -44,7 +45,7 @@ bool plan_partitions(const MeshHost& h, int k, int align, std::vector<PartPlan>&
     for (int r = 0; r <= k; ++r) b[r] = r == k ? ne : (ne * r / k) / align * align;
     for (int r = 0; r < k; ++r)
         if (b[r + 1] <= b[r]) {
-            err = "too many partitions for this mesh (every slab needs at least one 12-element tile)";
+            err = "too many partitions for this mesh (every slab needs at least 96 elements)";
             return false;
         }
     auto part_of = [&](int64_t g) {
@@ -90,6 +91,8 @@ bool plan_partitions(const MeshHost& h, int k, int align, std::vector<PartPlan>&
 }  // namespace dg
 
 namespace {
+
+constexpr int ALIGN = 96;   // slab boundaries: a common multiple of the kernels' tile sizes
 
 dg_status pfail(dg_status code, const std::string& msg) { return dg::set_error(code, msg.c_str()); }
 
@@ -197,7 +200,7 @@ dg_status dg_partition_create(dg_mesh* m, int k, void* stream, dg_partition** ou
     P->parent = m;
     P->k = k;
     std::string err;
-    if (!dg::plan_partitions(m->host, k, 12, P->plan, err)) {
+    if (!dg::plan_partitions(m->host, k, ALIGN, P->plan, err)) {
         free_partition(P);
         return pfail(DG_ERR_ARG, err);
     }
@@ -225,12 +228,9 @@ dg_status dg_partition_create(dg_mesh* m, int k, void* stream, dg_partition** ou
         sm->d_tab = m->d_tab;
         sm->d_tab64 = m->d_tab64;
         sm->d_tab16 = m->d_tab16;
-        sm->d_tabws = m->d_tabws;
         sm->d_fperm = m->d_fperm;
         sm->mix_inv_b1 = m->mix_inv_b1;
         sm->mix_inv_b2 = m->mix_inv_b2;
-        sm->ws_inv_b1 = m->ws_inv_b1;
-        sm->ws_inv_b2 = m->ws_inv_b2;
         sm->d_status = m->d_status;
         PTRY(upload_vec(&sm->d_nbr, sm->host.nbr, s));
         PTRY(upload_vec(&sm->d_fcode, sm->host.fcode, s));
@@ -290,7 +290,7 @@ dg_status dg_partition_plan(const int32_t* tet_vid, const double* tet_xyz, const
     std::string err;
     if (!dg::build_mesh(tet_vid, tet_xyz, bc_tag, ne, renumber, h, code, err)) return pfail((dg_status)code, err);
     std::vector<dg::PartPlan> plan;
-    if (!dg::plan_partitions(h, k, 12, plan, err)) return pfail(DG_ERR_ARG, err);
+    if (!dg::plan_partitions(h, k, ALIGN, plan, err)) return pfail(DG_ERR_ARG, err);
     const dg::PartPlan& pl = plan[r];
     if (first) *first = pl.first;
     if (count) *count = pl.count;

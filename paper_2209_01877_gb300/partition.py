@@ -3,7 +3,8 @@
 The paper renumbers its grid once before time stepping, for every process
 (Sec. III-B).  A partitioned run gives rank r the contiguous slab of the
 renumbered element order that ``dg_partition_plan`` assigns (slab boundaries
-on multiples of the mixed kernel's 12-element tile) and a halo: the other
+on multiples of 96 elements, a common multiple of the kernels' tile sizes)
+and a halo: the other
 ranks' elements that its own elements' faces reach.  Per residual evaluation
 a rank needs one halo exchange; the time step and the conserved totals are
 reduced over the ranks.

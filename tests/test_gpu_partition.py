@@ -2,8 +2,8 @@
 halo exchange by device gather, Sec. III-B's per-process grid): the
 residual through the partitions is bitwise the unpartitioned residual for
 every precision (each element's residual comes from the same inputs through
-the same kernel; slab boundaries on 12-element tiles keep the mixed kernel's
-tiles), the time-step minimum over the partitions equals dg_stable_dt
+the same kernel; slab boundaries on multiples of 96 elements keep every
+kernel's tiles), the time-step minimum over the partitions equals dg_stable_dt
 exactly, and the totals summed over the partitions equal dg_integrals to
 1e-13 (a different summation order)."""
 import numpy as np
@@ -46,7 +46,7 @@ def test_partitioned_residual_is_bitwise_the_whole_mesh_residual(precision, orde
         total = 0
         for r in range(k):
             first, count, ids, owners = dg.dg_partition_info(part, r)
-            assert first == total and first % 12 == 0
+            assert first == total and first % 96 == 0
             total += count
             assert len(ids) > 0 and np.all(owners != r)
         assert total == m.ne

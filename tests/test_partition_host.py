@@ -1,6 +1,6 @@
 """CPU checks of the partitioned layout (the multi-process form of the paper's
 per-process grid, Sec. III-B): the host-only plan covers the element order
-with contiguous slabs on 12-element boundaries and its halos are exactly the
+with contiguous slabs on 96-element boundaries and its halos are exactly the
 other slabs' face neighbours (recomputed from the oracle's face matching); and
 a world-size-2 gloo run exchanges the halo blocks and reduces the time-step
 minimum and the conserved totals over the ranks."""
@@ -40,7 +40,7 @@ def test_plan_slabs_and_halos(renumber, kind, k):
     for r in range(k):
         first, count, ids, part = dg.dg_partition_plan(m.tet_vid, m.tet_xyz, tag, renumber, k, r)
         assert first == end and count > 0
-        assert first % 12 == 0
+        assert first % 96 == 0
         end = first + count
         own = np.zeros(m.ne, dtype=bool)
         own[first:end] = True
@@ -56,10 +56,10 @@ def test_plan_slabs_and_halos(renumber, kind, k):
 
 
 def test_plan_rejects_too_many_partitions():
-    m = I.make_periodic_cube(3, jitter=0.1)                       # 162 elements: 13.5 tiles of 12
-    dg.dg_partition_plan(m.tet_vid, m.tet_xyz, None, dg.DG_ORDER_RCM, 13, 0)
+    m = I.make_periodic_cube(4, jitter=0.1)                       # 384 elements: 4 slabs of 96
+    dg.dg_partition_plan(m.tet_vid, m.tet_xyz, None, dg.DG_ORDER_RCM, 4, 0)
     with pytest.raises(dg.DGError) as e:
-        dg.dg_partition_plan(m.tet_vid, m.tet_xyz, None, dg.DG_ORDER_RCM, 14, 0)
+        dg.dg_partition_plan(m.tet_vid, m.tet_xyz, None, dg.DG_ORDER_RCM, 5, 0)
     assert e.value.status == 1
 
 
