@@ -33,7 +33,7 @@ def _internal_neighbours(m, renumber):
 @pytest.mark.parametrize("kind", ["periodic", "box"])
 @pytest.mark.parametrize("k", [2, 3, 4])
 def test_plan_slabs_and_halos(renumber, kind, k):
-    m = I.make_periodic_cube(4, jitter=0.15) if kind == "periodic" else I.make_box_channel(4, 3, 3, jitter=0.15)
+    m = I.make_periodic_cube(5, jitter=0.15) if kind == "periodic" else I.make_box_channel(6, 4, 4, jitter=0.15)
     tag = None if kind == "periodic" else m.bc_tag
     nbr, _ = _internal_neighbours(m, renumber)
     end = 0
