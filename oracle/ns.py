@@ -21,9 +21,13 @@ What it follows (arXiv:2209.01877):
 Readings (the paper is silent or garbled on these):
   N1  the equation of state p = rho R T with R = 1 (T = p / rho in the nondimensional form),
       c_p = gamma R / (gamma - 1), kappa = mu c_p / Pr; mu and Pr are constants.
-  N2  Qhat on a boundary face of the gradient equation is the interior trace Q- (the viscous
-      boundary conditions themselves are not part of this oracle: the viscous residual is
-      defined on meshes without boundary faces, i.e. periodic ones).
+  N2  boundary faces of the gradient equation: on a wall (bc tag 1) Qhat is the no-slip
+      adiabatic wall state Q_b = (rho-, 0, 0, 0, E- - |m-|^2 / (2 rho-)) -- the interior
+      density and internal energy at rest; on a far-field face (bc tag 2) Qhat = Q-.
+  N5  viscous flux on boundary faces: on a wall H_v = F_v(Q_b, Z-) . n with its energy
+      component set to zero (adiabatic: no heat flux, and a wall at rest does no work); on a
+      far-field face H_v = F_v(Q-, Z-) . n.  The inviscid flux of a wall face keeps the Euler
+      wall ghost (mirror state: no mass flux, the pressure force).
   N3  the garbled off-diagonal stress of the paper (mu_y + mu_x for velocity components mu, nu)
       is read as the symmetric tau_xy = mu (du/dy + dv/dx) of Stokes' hypothesis.
   N4  Z is the gradient of the conserved variables (the paper's Z = grad Q); velocity and
@@ -34,6 +38,10 @@ Readings (the paper is silent or garbled on these):
 
 Parity status: pinned by tests/test_oracle_ns.py:
   * the BR1 gradient is exact for polynomial states;
+  * the domain integral of Z equals the boundary integral of Qhat n (the wall state of N2),
+    with closed-form values on a wall-bounded shear flow;
+  * the wall drag of plane Poiseuille flow is the exact -2 mu U0 per unit wall area pair,
+    and the adiabatic wall passes no energy;
   * the chain rule and the viscous flux match complex-step derivatives of analytic fields;
   * discrete conservation holds on periodic meshes;
   * a uniform state has zero viscous residual;
@@ -46,6 +54,7 @@ import numpy as np
 
 from .dg import CHUNK, Problem, _es
 from .mesh import face_normal_area
+from .euler import BC_FARFIELD, BC_WALL
 
 
 def primitive_gradients(U, Z, gamma, R=1.0):
@@ -65,6 +74,14 @@ def primitive_gradients(U, Z, gamma, R=1.0):
     T = p / (rho * R)
     dT = (dp - (T * R)[..., None] * drho) / (rho * R)[..., None]
     return u, du, T, dT
+
+
+def wall_state(U):
+    """No-slip adiabatic wall state Q_b [..., 5] from the interior trace U (reading N2)."""
+    Q = np.zeros_like(U)
+    Q[..., 0] = U[..., 0]
+    Q[..., 4] = U[..., 4] - 0.5 * np.sum(U[..., 1:4] ** 2, axis=-1) / U[..., 0]
+    return Q
 
 
 def viscous_flux(U, Z, mu, kappa, gamma, R=1.0):
@@ -117,7 +134,10 @@ class NSProblem(Problem):
             for f in range(4):
                 n, area = face_normal_area(self.xyz, e, f)
                 Um, Up, inner = self._traces(U, e, f)
-                Qhat = np.where(inner[:, None, None], 0.5 * (Um + Up), Um)     # reading N2 on boundaries
+                Qhat = 0.5 * (Um + Up)
+                Qhat[~inner] = Um[~inner]                                    # far field (reading N2)
+                wall = ~inner & (self.btype[e, f] == BC_WALL)
+                Qhat[wall] = wall_state(Um[wall])                            # wall (reading N2)
                 rhs += _es("q,e,eqv,ed,qj->edvj", self.wf, 2.0 * area, Qhat, n, self.phi_f[f])
             M = self.mass(e)
             for d in range(3):
@@ -136,12 +156,17 @@ class NSProblem(Problem):
         for f in range(4):
             n, area = face_normal_area(self.xyz, e, f)
             Um, Up, inner = self._traces(U, e, f)
-            if not np.all(inner):
-                raise ValueError("the viscous residual is defined on meshes without boundary faces")
             Zm, Zp, _ = self._traces(Z, e, f)
             Fm = viscous_flux(Um, Zm, self.mu, self.kappa, self.gamma, self.R)
             Fp = viscous_flux(Up, Zp, self.mu, self.kappa, self.gamma, self.R)
-            Hv = _es("eqdv,ed->eqv", 0.5 * (Fm + Fp), n)
+            Fh = 0.5 * (Fm + Fp)
+            Fh[~inner] = Fm[~inner]                                         # far field (reading N5)
+            wall = ~inner & (self.btype[e, f] == BC_WALL)
+            if np.any(wall):
+                Fw = viscous_flux(wall_state(Um[wall]), Zm[wall], self.mu, self.kappa, self.gamma, self.R)
+                Fw[..., 4] = 0.0                                            # adiabatic wall (reading N5)
+                Fh[wall] = Fw
+            Hv = _es("eqdv,ed->eqv", Fh, n)
             rhs += _es("q,e,eqv,qj->evj", self.wf, 2.0 * area, Hv, self.phi_f[f])
         return rhs
 
@@ -159,4 +184,4 @@ class NSProblem(Problem):
         return out
 
 
-__all__ = ["NSProblem", "primitive_gradients", "viscous_flux"]
+__all__ = ["NSProblem", "primitive_gradients", "viscous_flux", "wall_state"]

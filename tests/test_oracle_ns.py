@@ -8,6 +8,10 @@
 - Free stream: a uniform state has zero gradient and zero viscous residual.
 - Consistency: the viscous part of the residual of a shear wave converges to mu d2u/dy2 at
   order p - 1.
+- Boundaries (readings N2, N5): with the constant test function the gradient equation gives
+  int Z dx = boundary integral of Qhat n, and the viscous residual gives int R_v dx = boundary
+  integral of H_v; closed forms on channels with no-slip walls (a wall-bounded shear flow,
+  plane Poiseuille flow) and with far-field ends (a quadratic stretching flow).
 """
 import itertools
 import math
@@ -16,7 +20,7 @@ import numpy as np
 import pytest
 
 from oracle.dg import Problem
-from oracle.ns import NSProblem, primitive_gradients, viscous_flux
+from oracle.ns import NSProblem, primitive_gradients, viscous_flux, wall_state
 from paper_2209_01877_gb300 import inputs as I
 
 GAMMA = 1.4
@@ -44,7 +48,10 @@ def _poly_grad(x, coef, exps, d):
 @pytest.mark.parametrize("p", [1, 2, 3])
 def test_br1_gradient_exact_for_polynomial_states(p):
     m = I.make_box_channel(3, 2, 2, lengths=(1.5, 1.0, 1.0), jitter=0.15)
-    P = NSProblem(m.tet_vid, m.tet_xyz, m.bc_tag, p=p, freestream=I.freestream_state(0.3), mu=0.01)
+    # every boundary face far field: there Qhat is the interior trace, which for one polynomial
+    # over the mesh is the exact value (a no-slip wall imposes its own state instead)
+    bc = np.where(m.bc_tag != 0, 2, 0).astype(np.int8)
+    P = NSProblem(m.tet_vid, m.tet_xyz, bc, p=p, freestream=I.freestream_state(0.3), mu=0.01)
     rng = np.random.default_rng(5)
     exps = _monomials(p)
     coef = rng.uniform(-1.0, 1.0, size=(5, len(exps)))
@@ -175,3 +182,78 @@ def test_shear_wave_viscous_term_converges(p):
     # a wrong viscosity factor, a doubled or dropped face term leaves an O(1) relative error
     assert e8 < 0.1
     assert e4 / e8 > 2.0 ** (p - 1.3)
+
+
+def _domain_integral(P, A):
+    """int over the mesh of the modal field A [ne, 5, nb], per variable (FP64 quadrature)."""
+    return np.einsum("q,e,qj,evj->v", P.wq, P.det, P.phi_q, A)
+
+
+def _field(rho, u, p):
+    """Conserved state from primitive fields (arrays over the points)."""
+    z = np.zeros_like(rho)
+    E = p / (GAMMA - 1.0) + 0.5 * rho * u * u
+    return np.stack([rho, rho * u, z, z, E], axis=-1)
+
+
+def test_wall_state():
+    U = np.array([[1.2, 0.3, -0.6, 0.24, 3.0]])
+    Q = wall_state(U)
+    np.testing.assert_array_equal(Q[0, 1:4], 0.0)
+    assert Q[0, 0] == 1.2
+    assert abs(Q[0, 4] - (3.0 - 0.5 * (0.09 + 0.36 + 0.0576) / 1.2)) < 1e-15
+
+
+def test_gradient_boundary_integral_with_no_slip_walls():
+    """Walls at y = 0, 1 (periodic in x, z); rho = 1 + y/2, u = U0 (1 + y), p = p0 (all exactly
+    represented at P3).  int Z_y dx = (Q_b(1) - Q_b(0)) Lx Lz with the wall state Q_b = (rho, 0, 0,
+    0, p0 / (gamma - 1)): only the density differs, by 1/2.  Taking the trace itself on the wall
+    would give 2 U0 in the x-momentum and a non-zero energy entry."""
+    Lx, Lz, U0, p0 = 1.5, 1.2, 0.4, 0.8
+    m = I.make_box_mesh((3, 3, 3), lengths=(Lx, 1.0, Lz), periodic=(True, False, True), jitter=0.15)
+    P = NSProblem(m.tet_vid, m.tet_xyz, m.bc_tag, p=3, mu=0.02)
+    U = P.project(lambda x: _field(1.0 + 0.5 * x[..., 1], U0 * (1.0 + x[..., 1]), np.full(x.shape[:-1], p0)))
+    Z = P.gradient(U)
+    area = Lx * Lz
+    np.testing.assert_allclose(_domain_integral(P, Z[:, 0]), 0.0, atol=1e-12)
+    np.testing.assert_allclose(_domain_integral(P, Z[:, 2]), 0.0, atol=1e-12)
+    np.testing.assert_allclose(_domain_integral(P, Z[:, 1]), [0.5 * area, 0, 0, 0, 0], atol=1e-12)
+
+
+def test_poiseuille_wall_drag_and_adiabatic_walls():
+    """Plane Poiseuille profile u = U0 y (1 - y) between no-slip walls at y = 0, 1, rho = 1, p
+    uniform, P2 (u exact; the energy only approximately).  The viscous x-momentum residual
+    integrates to the wall shear -mu du/dy|_0 + mu du/dy|_1 = -2 mu U0 per unit wall area (BR1 keeps
+    the exact gradient: the profile satisfies no-slip); the adiabatic walls pass no energy and the
+    mass flux is zero.  Half the wall flux, the wrong normal, or heat conducted through the
+    wall each break one of these."""
+    Lx, Lz, U0, mu = 1.5, 1.2, 0.5, 0.05
+    m = I.make_box_mesh((3, 3, 3), lengths=(Lx, 1.0, Lz), periodic=(True, False, True), jitter=0.15)
+    P = NSProblem(m.tet_vid, m.tet_xyz, m.bc_tag, p=2, flux="roe", mu=mu)
+    one = lambda x: np.ones(x.shape[:-1])
+    U = P.project(lambda x: _field(one(x), U0 * x[..., 1] * (1.0 - x[..., 1]), 0.7 * one(x)))
+    Rv = P.ns_residual(U) - Problem(m.tet_vid, m.tet_xyz, m.bc_tag, p=2, flux="roe").residual(U)
+    tot = _domain_integral(P, Rv)
+    expect = -2.0 * mu * U0 * Lx * Lz
+    assert abs(tot[1] - expect) < 1e-12
+    np.testing.assert_allclose(tot[[0, 2, 3, 4]], 0.0, atol=1e-13)
+    # the energy entry is zero by the adiabatic condition, not by accident: the discrete
+    # temperature gradient on the walls is not zero (the quartic energy is projected to P2)
+    Z = P.gradient(U)
+    assert np.abs(Z[:, 1, 4]).max() > 1e-3
+
+
+def test_far_field_viscous_flux_one_sided():
+    """Far-field ends at x = 0, Lx (periodic in y, z); rho = 1, u = a x^2, p uniform (P2).  The
+    normal stress tau_xx = (4/3) mu du/dx = (8/3) mu a x, so the x-momentum viscous residual
+    integrates to (8/3) mu a Lx Ly Lz, all through the outflow end; H_v = F_v(Q-, Z-) . n there."""
+    Lx, Ly, Lz, a, mu = 1.5, 1.0, 1.2, 0.2, 0.03
+    m = I.make_box_mesh((3, 3, 3), lengths=(Lx, Ly, Lz), periodic=(False, True, True), jitter=0.15)
+    fs = I.freestream_state(0.3)
+    P = NSProblem(m.tet_vid, m.tet_xyz, m.bc_tag, p=2, flux="roe", freestream=fs, mu=mu)
+    one = lambda x: np.ones(x.shape[:-1])
+    U = P.project(lambda x: _field(one(x), a * x[..., 0] ** 2, 0.7 * one(x)))
+    Rv = P.ns_residual(U) - Problem(m.tet_vid, m.tet_xyz, m.bc_tag, p=2, flux="roe", freestream=fs).residual(U)
+    tot = _domain_integral(P, Rv)
+    assert abs(tot[1] - (8.0 / 3.0) * mu * a * Lx * Ly * Lz) < 1e-12
+    np.testing.assert_allclose(tot[[0, 2, 3]], 0.0, atol=1e-13)
