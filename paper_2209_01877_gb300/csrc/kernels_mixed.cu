@@ -124,15 +124,15 @@ struct SPlan {
     static constexpr int ELW = 56;
     // shared memory (bytes): tables, then one region per context
     static constexpr int SZ_T1 = 2 * N1 * K1 * 2, SZ_T2 = 2 * N2 * K2 * 2;
-    // operand union of a context: A1 (build .. MMA 1), then A2 (flux phase .. MMA 2)
+    // operands of a context: A1 (the next tile's rows are built while MMA 2 reads A2)
     static constexpr int SZ_A1 = 64 * K1 * 2, SZ_C = SLOTS * NV5 * 4, SZ_A2 = 64 * K2 * 2;
-    static constexpr int SZ_AU = SZ_A1 > SZ_A2 ? SZ_A1 : SZ_A2;
     static constexpr int SZ_PF = 4 * NQF * NB * 4;                         // FP32 face-point basis [f][p][j]
     static constexpr int O_T1 = 0, O_T2 = a128(O_T1 + SZ_T1), O_PF = a128(O_T2 + SZ_T2);
     static constexpr int O_CTX = a128(O_PF + SZ_PF);
     // context-relative offsets
-    static constexpr int X_AU = 0;
-    static constexpr int X_SU = a128(X_AU + SZ_AU);                        // float [ET][5][VSTR]
+    static constexpr int X_A1 = 0;
+    static constexpr int X_A2 = a128(X_A1 + SZ_A1);
+    static constexpr int X_SU = a128(X_A2 + SZ_A2);                        // float [ET][5][VSTR]
     static constexpr int X_SN = a128(X_SU + ET * USTR * 4);                // float [SLOTS][5][NQF4]
     static constexpr int X_ROW = a128(X_SN + SLOTS * 5 * NQF4 * 4);       // float2 [64] (mean, factor)
     // per slot, 3 float4: (n, sc), (sc Fbar.n)[0..3], ((sc Fbar.n)[4], staging offset, first K word, -)
@@ -140,7 +140,11 @@ struct SPlan {
     static constexpr int X_EL = a128(X_REC + SLOTS * 48);                 // float [ET][ELW]
     static constexpr int X_CODE = a128(X_EL + ET * ELW * 4);              // uint32 [SLOTS]
     static constexpr int X_LIST = X_CODE + SLOTS * 4;                      // uint8 [2*SLOTS]: cross, work
-    static constexpr int X_C = a128(X_LIST + 2 * SLOTS);                   // float [SLOTS][5 Nb] neighbour blocks
+    // int [THDR] header of the staged tile; int [SLOTS + 1] neighbour ids and cross count of the
+    // tile whose neighbour blocks are copied next
+    static constexpr int X_HDR = a128(X_LIST + 2 * SLOTS);
+    static constexpr int X_XN = X_HDR + 16;
+    static constexpr int X_C = a128(X_XN + (SLOTS + 1) * 4);                // float [SLOTS][5 Nb] neighbour blocks
     static constexpr int X_MB = a128(X_C + SZ_C);                          // mbarrier, then the drain mbarrier
     static constexpr int CTX_BYTES = a128(X_MB + 16);
     static constexpr int O_PERM = O_CTX + 2 * CTX_BYTES;                   // int8 [6][NQF]
@@ -216,6 +220,47 @@ __device__ __forceinline__ void issue_neighbour_blocks(const StageArgs& a, int64
     tc::cp_async_commit();
 }
 
+// a tile's operand rows of MMA 1 (threads 0..63), its slot codes and lists (threads 80..127) and
+// header (threads 64, 65) into the context's buffers
+template <int NB, int K1, bool BF>
+__device__ __forceinline__ void stage_tile_inputs(const StageArgs& a, int64_t tile, int ct, __half* sA1, float2* sRow,
+                                                  uint32_t* sCode, uint8_t* sList, int* sHdr) {
+    const int64_t e0 = tile * ET;
+    const int nel = (a.ne - e0) < (int64_t)ET ? (int)(a.ne - e0) : ET;
+    if (ct < 64) {
+        const int r = ct;
+        if (r < 5 * nel) {
+            const int e = r / 5, v = r - 5 * e;
+            sRow[r] = build_row<NB, K1, BF>(a.U_hi + ((e0 + e) * 5 + v) * NB, sA1, r, a.inv_beta1);
+        } else {
+            zero_row(sA1, r, K1);
+        }
+    } else if (ct < 64 + THDR) {
+        sHdr[ct - 64] = __ldg(a.thdr + tile * THDR + (ct - 64));
+    } else if (ct >= 80 && ct < 80 + SLOTS) {
+        const int t2 = ct - 80;
+        const uint8_t* tl = a.tlist + tile * (2 * SLOTS);
+        sCode[t2] = __ldg(a.slot + tile * SLOTS + t2);
+        sList[t2] = __ldg(tl + t2);
+        sList[SLOTS + t2] = __ldg(tl + SLOTS + t2);
+    }
+}
+
+// the copies of a tile's neighbour blocks from staged ids (threads 128..255)
+template <int NV5>
+__device__ __forceinline__ void issue_staged_blocks(const StageArgs& a, const int* sXn, int ct, float* sC) {
+    constexpr int VW = NV5 % 4 == 0 ? 4 : 2;
+    constexpr int NU = NV5 / VW;
+    const int ncross = sXn[SLOTS];
+    for (int i = ct - 128; i < ncross * NU; i += CT - 128) {
+        const int c = i / NU, u = i - c * NU;
+        const float* src = a.U_hi + (int64_t)sXn[c] * NV5 + u * VW;
+        if constexpr (VW == 4) tc::cp_async16(sC + c * NV5 + 4 * u, src);
+        else cp_async8(sC + c * NV5 + 2 * u, src);
+    }
+    tc::cp_async_commit();
+}
+
 template <int P, int FLUX, bool BF>
 __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     using S = SPlan<P>;
@@ -230,9 +275,9 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     const __half* sT1b = sT1a + N1 * K1;
     const __half* sT2a = reinterpret_cast<const __half*>(smem + S::O_T2);
     unsigned char* cx = smem + S::O_CTX + ctx * S::CTX_BYTES;
-    __half* sA1 = reinterpret_cast<__half*>(cx + S::X_AU);
+    __half* sA1 = reinterpret_cast<__half*>(cx + S::X_A1);
     float* sC = reinterpret_cast<float*>(cx + S::X_C);   // neighbour coefficient blocks (next tile's in flight)
-    __half* sA2 = reinterpret_cast<__half*>(cx + S::X_AU);
+    __half* sA2 = reinterpret_cast<__half*>(cx + S::X_A2);
     const float* sPhiF = reinterpret_cast<const float*>(smem + S::O_PF);
     float* sU = reinterpret_cast<float*>(cx + S::X_SU);
     float* sN = reinterpret_cast<float*>(cx + S::X_SN);
@@ -241,6 +286,8 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     float* sEl = reinterpret_cast<float*>(cx + S::X_EL);
     uint32_t* sCode = reinterpret_cast<uint32_t*>(cx + S::X_CODE);
     uint8_t* sList = reinterpret_cast<uint8_t*>(cx + S::X_LIST);
+    int* sHdr = reinterpret_cast<int*>(cx + S::X_HDR);
+    int* sXn = reinterpret_cast<int*>(cx + S::X_XN);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(cx + S::X_MB);
     const int8_t* sPerm = reinterpret_cast<const int8_t*>(smem + S::O_PERM);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::O_SLOT);
@@ -284,56 +331,27 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
 
     const int64_t ntiles = (a.ne + ET - 1) / ET;
     const int64_t tstride = 2 * (int64_t)gridDim.x;
-    // the first tile's neighbour blocks; later tiles' are issued one tile ahead, during MMA 2
-    if (ct >= 128 && 2 * (int64_t)blockIdx.x + ctx < ntiles)
-        issue_neighbour_blocks<NV5>(a, 2 * (int64_t)blockIdx.x + ctx, ct, sC);
-    for (int64_t tile = 2 * (int64_t)blockIdx.x + ctx; tile < ntiles; tile += tstride) {
+    const int64_t tfirst = 2 * (int64_t)blockIdx.x + ctx;
+    // prologue: the first tile's operand rows, metadata and neighbour blocks.  Later tiles' are
+    // prepared during the previous tile: neighbour ids while MMA 1 runs, the block copies after
+    // the traces, the operand rows and metadata while MMA 2 runs
+    if (tfirst < ntiles) {
+        stage_tile_inputs<NB, K1, BF>(a, tfirst, ct, sA1, sRow, sCode, sList, sHdr);
+        if (ct >= 128) {
+            issue_neighbour_blocks<NV5>(a, tfirst, ct, sC);
+            tc::cp_async_wait_all();
+        }
+    }
+    tc::fence_async_smem();
+    tc::fence_before();
+    ctx_sync(bar_id);
+    tc::fence_after();
+    for (int64_t tile = tfirst; tile < ntiles; tile += tstride) {
         const int64_t e0 = tile * ET;
         const int nel = (a.ne - e0) < (int64_t)ET ? (int)(a.ne - e0) : ET;
-        const int32_t* hdr = a.thdr + tile * THDR;
-        const int ncross = __ldg(hdr), nwork = __ldg(hdr + 1);
-        // ---- L2 prefetch of this context's next tile (contiguous blocks) ---------------------------
-        if (ct == 0) {
-            const int64_t nt = tile + tstride;
-            if (nt < ntiles) {
-                const int64_t n0 = nt * ET;
-                const int nn = (a.ne - n0) < (int64_t)ET ? (int)(a.ne - n0) : ET;
-                const uint32_t sb = (uint32_t)(nn * 5 * NB * 4);
-                prefetch_l2(a.U_hi + n0 * 5 * NB, sb);
-                if (a.mode != 0) {
-                    prefetch_l2(a.U_lo + n0 * 5 * NB, sb);
-                    if (a.a != 0.f) {
-                        prefetch_l2(a.U0_hi + n0 * 5 * NB, sb);
-                        prefetch_l2(a.U0_lo + n0 * 5 * NB, sb);
-                    }
-                }
-                prefetch_l2(a.jinv + n0 * 9, (uint32_t)(nn * 36));
-                prefetch_l2(a.xnbr + nt * SLOTS, SLOTS * 4);
-                prefetch_l2(a.slot + nt * SLOTS, SLOTS * 4);
-            }
-        }
-        // ---- build: operand rows, per-element quantities, tile metadata ---------------------------
-        if (ct < 64) {
-            const int r = ct;
-            if (r < 5 * nel) {
-                const int e = r / 5, v = r - 5 * e;
-                sRow[r] = build_row<NB, K1, BF>(a.U_hi + ((e0 + e) * 5 + v) * NB, sA1, r, a.inv_beta1);
-            } else {
-                zero_row(sA1, r, K1);
-            }
-        } else if (ct >= 80 && ct < 80 + SLOTS) {
-            const int t2 = ct - 80;
-            const uint8_t* tl = a.tlist + tile * (2 * SLOTS);
-            sCode[t2] = __ldg(a.slot + tile * SLOTS + t2);
-            sList[t2] = __ldg(tl + t2);
-            sList[SLOTS + t2] = __ldg(tl + SLOTS + t2);
-        } else if (ct >= 128) {
-            tc::cp_async_wait_all();   // this tile's neighbour blocks (issued a tile ahead) have landed
-        }
-        tc::fence_async_smem();
-        tc::fence_before();
-        ctx_sync(bar_id);
-        tc::fence_after();
+        const int ncross = sHdr[0], nwork = sHdr[1];
+        const int64_t nt = tile + tstride;   // this context's next tile
+        const bool has_next = nt < ntiles;
         // ---- MMA 1: own values at all points, neighbours' traces ----------------------------------
         // D = A x [phi_hi, phi_hi] + A x [phi_lo, 0] = (x_hi + x_lo) phi_hi + x_hi phi_lo
         if (ct == 0) {
@@ -348,6 +366,31 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 for (int ks = 0; ks < K1 / 16; ++ks)
                     tc::mma(tmem + S::C_D1, dA1 + KSTEP * ks, dT1[h] + KSTEP * ks, id1, (h | ks) != 0);
             tc::commit(mbar);
+        }
+        // the next tile: neighbour ids and cross count into sXn (loads issued here, stored after
+        // this thread's traces), and an L2 prefetch of its contiguous blocks
+        int xn0 = 0, xn1 = 0, xnc = 0;
+        if (ct >= CT - 32 && has_next) {
+            const int i = ct - (CT - 32);
+            xn0 = __ldg(a.xnbr + nt * SLOTS + i);
+            if (i + 32 < SLOTS) xn1 = __ldg(a.xnbr + nt * SLOTS + i + 32);
+            if (i == 0) {
+                xnc = __ldg(a.thdr + nt * THDR);
+                const int64_t n0 = nt * ET;
+                const int nn = (a.ne - n0) < (int64_t)ET ? (int)(a.ne - n0) : ET;
+                const uint32_t sb = (uint32_t)(nn * 5 * NB * 4);
+                prefetch_l2(a.U_hi + n0 * 5 * NB, sb);
+                if (a.mode != 0) {
+                    prefetch_l2(a.U_lo + n0 * 5 * NB, sb);
+                    if (a.a != 0.f) {
+                        prefetch_l2(a.U0_hi + n0 * 5 * NB, sb);
+                        prefetch_l2(a.U0_lo + n0 * 5 * NB, sb);
+                    }
+                }
+                prefetch_l2(a.jinv + n0 * 9, (uint32_t)(nn * 36));
+                prefetch_l2(a.slot + nt * SLOTS, SLOTS * 4);
+                prefetch_l2(a.tlist + nt * (2 * SLOTS), 2 * SLOTS);
+            }
         }
         // the neighbours' traces at their face points (FP32, own point order of the neighbour's
         // face), while the tensor cores work: thread per (cross index, point)
@@ -420,11 +463,19 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 for (int v = 0; v < 5; ++v) el[50 + v] = __int_as_float(rowpart(e * 5 + v, K2));
             }
         }
+        if (ct >= CT - 32 && has_next) {
+            const int i = ct - (CT - 32);
+            sXn[i] = xn0;
+            if (i + 32 < SLOTS) sXn[i + 32] = xn1;
+            if (i == 0) sXn[SLOTS] = xnc;
+        }
         if (!tc_wait(mbar, phase, ct, bar_id)) {
             if (ct == 0) atomicOr(a.status, 2u);
             break;
         }
         tc::fence_after();
+        // the next tile's neighbour blocks (sC is free: this tile's traces are done)
+        if (ct >= 128 && has_next) issue_staged_blocks<NV5>(a, sXn, ct, sC);
         // per face (before the staging): outward normal, |grad lambda_f| times the element's
         // flux scale, and the mean state's scaled normal flux
         if (ct < SLOTS) {
@@ -558,8 +609,9 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                         ks >= S::NCH);
             tc::commit(mbar);
         }
-        // the next tile's neighbour blocks (sC is free: this tile's traces are done)
-        if (ct >= 128 && tile + tstride < ntiles) issue_neighbour_blocks<NV5>(a, tile + tstride, ct, sC);
+        // the next tile's operand rows and metadata (A1, the rows, codes and lists are free: MMA 1
+        // and the flux phase are done)
+        if (has_next) stage_tile_inputs<NB, K1, BF>(a, nt, ct, sA1, sRow, sCode, sList, sHdr);
         // epilogue operands in flight while the tensor cores work.  This thread holds rows rA, rB
         // (16-lane layout) and, per column group g of its part, the mode pair (or single mode) below:
         //   part 0: modes cb, cb+1 (columns 0..7);
@@ -597,6 +649,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 }
             }
         }
+        if (ct >= 128) tc::cp_async_wait_all();   // the next tile's neighbour blocks have landed
         if (!tc_wait(mbar, phase, ct, bar_id)) {
             if (ct == 0) atomicOr(a.status, 2u);
             break;
@@ -666,6 +719,7 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 }
             }
         }
+        tc::fence_async_smem();   // the next tile's A1 rows, written above, are read by MMA 1
         tc::fence_before();
         ctx_sync(bar_id);
         tc::fence_after();
