@@ -629,9 +629,7 @@ def run_study(args):
         out.update({"stable_dt_ms_incl_sync": t_dt * 1e3, "integrals_ms_incl_sync": t_int * 1e3,
                     "tets": mesh.ne})
     elif args.study == "ns":
-        if w["box"]:
-            raise SystemExit("the Navier-Stokes residual needs a periodic workload")
-        M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, None, order=p, precision=dg.DG_FP64, flux=fl)
+        M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, tag, order=p, precision=dg.DG_FP64, flux=fl, freestream=fs)
         U = torch.from_numpy(M.project(field)).cuda()
         R = torch.empty_like(U)
         n = max(args.steps, 3)

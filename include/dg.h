@@ -158,10 +158,16 @@ dg_status dg_residual(dg_mesh* mesh, const double* U, double* R, void* stream);
  * term and the central viscous face flux.  Viscous flux of Eq. 1 in 3D with
  * Stokes' stress, constant viscosity mu >= 0 and Prandtl number prandtl > 0,
  * gas constant 1 (T = p / rho), conduction coefficient
- * mu gamma / ((gamma - 1) prandtl).  U and R as for dg_residual (device,
- * caller order; U NULL = the internal state).  FP64 meshes without boundary
- * faces only (else DG_ERR_UNSUPPORTED).  The first call with mu > 0 allocates
- * the gradient buffer (15 Nb doubles per element), owned by the mesh. */
+ * mu gamma / ((gamma - 1) prandtl).  Boundary faces: a DG_BC_WALL face is a
+ * no-slip adiabatic wall for the viscous lines (the gradient's central value
+ * there is the wall state: interior density and internal energy at rest; the
+ * viscous flux is F_v(wall state, interior gradient) . n with no energy flux)
+ * and keeps the Euler wall flux; a DG_BC_FARFIELD face takes the interior
+ * trace and the interior viscous flux.  U and R as for dg_residual (device,
+ * caller order; U NULL = the internal state).  FP64 meshes only (else
+ * DG_ERR_UNSUPPORTED).  The first call with mu > 0 allocates the gradient
+ * buffer (15 Nb doubles per element) and a face-flux buffer (16 Nqf doubles
+ * per element), both owned by the mesh. */
 dg_status dg_ns_residual(dg_mesh* mesh, const double* U, double* R, double mu, double prandtl, void* stream);
 
 /* One SSP-RK3 stage on the internal state, fused with the residual (one

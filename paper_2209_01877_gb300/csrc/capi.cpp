@@ -73,6 +73,7 @@ void free_mesh(dg_mesh* m) {
     for (auto& b : m->d_W) cudaFree(b);
     cudaFree(m->d_io);
     cudaFree(m->d_Z);
+    cudaFree(m->d_HB);
     if (m->rk_exec) cudaGraphExecDestroy(m->rk_exec);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     cudaFree(m->d_red);
@@ -369,8 +370,6 @@ dg_status dg_ns_residual(dg_mesh* m, const double* U, double* R, double mu, doub
     if (!m || !R) return fail(DG_ERR_ARG, "mesh and R must be non-NULL");
     if (!(mu >= 0.0) || !(prandtl > 0.0)) return fail(DG_ERR_ARG, "mu must be >= 0 and prandtl > 0");
     if (m->precision != DG_FP64) return fail(DG_ERR_UNSUPPORTED, "the Navier-Stokes residual runs on FP64 meshes");
-    if (m->host.n_bfaces > 0)
-        return fail(DG_ERR_UNSUPPORTED, "the Navier-Stokes residual needs a mesh without boundary faces");
     if (!U && !m->has_state) return fail(DG_ERR_NOSTATE, "no state set and U is NULL");
     dg_status st = ensure_work_buffers(m);
     if (st != DG_OK) return st;
@@ -383,8 +382,9 @@ dg_status dg_ns_residual(dg_mesh* m, const double* U, double* R, double mu, doub
     DG_CUDA(dg::launch_residual(m, in, nullptr, m->d_W[1], 0, 0.0, 0.0, 0.0, s));
     if (mu > 0.0) {
         if (!m->d_Z) DG_CUDA(cudaMalloc(&m->d_Z, (size_t)m->host.ne * 15 * m->nb * sizeof(double)));
-        DG_CUDA(dg::launch_ns_viscous(m, static_cast<const double*>(in), m->d_Z, static_cast<double*>(m->d_W[1]), mu,
-                                      prandtl, s));
+        if (!m->d_HB) DG_CUDA(cudaMalloc(&m->d_HB, dg::ns_face_buffer_doubles(m->p, m->host.ne) * sizeof(double)));
+        DG_CUDA(dg::launch_ns_viscous(m, static_cast<const double*>(in), m->d_Z, m->d_HB,
+                                      static_cast<double*>(m->d_W[1]), mu, prandtl, s));
     }
     DG_CUDA(dg::launch_scatter(m, m->d_W[1], R, s));
     return DG_OK;

@@ -82,6 +82,7 @@ struct dg_mesh {
     double* h_red = nullptr;       // pinned host reduction result
     unsigned int* d_status = nullptr;
     double* d_Z = nullptr;         // Navier-Stokes auxiliary gradient [ne][3][5][Nb] (lazy)
+    double* d_HB = nullptr;        // Navier-Stokes own viscous face fluxes [ne][4][Nqf][4] (lazy)
     // small meshes: a CUDA graph of several captured RK3 steps at one dt (dg_rk3_step)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t rk_exec = nullptr;
@@ -96,8 +97,9 @@ cudaError_t launch_residual(dg_mesh* m, const void* U, const void* U0, void* out
 cudaError_t launch_gather(dg_mesh* m, const double* user, void* internal, cudaStream_t s);   // caller -> internal
 // Navier-Stokes lines (FP64, no boundary faces): the BR1 gradient into Z, then the viscous
 // volume and face terms added to the residual R (internal order)
-cudaError_t launch_ns_viscous(dg_mesh* m, const double* U, double* Z, double* R, double mu, double prandtl,
-                              cudaStream_t s);
+cudaError_t launch_ns_viscous(dg_mesh* m, const double* U, double* Z, double* HB, double* R, double mu,
+                              double prandtl, cudaStream_t s);
+size_t ns_face_buffer_doubles(int p, int64_t ne);
 cudaError_t launch_scatter(dg_mesh* m, const void* internal, double* user, cudaStream_t s);  // internal -> caller
 cudaError_t launch_scatter_f32(dg_mesh* m, const float* internal, double* user, cudaStream_t s);
 cudaError_t launch_stable_dt(dg_mesh* m, const void* U, double* d_out, cudaStream_t s);

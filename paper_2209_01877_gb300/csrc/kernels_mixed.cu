@@ -220,25 +220,26 @@ __device__ __forceinline__ void issue_neighbour_blocks(const StageArgs& a, int64
     tc::cp_async_commit();
 }
 
-// a tile's operand rows of MMA 1 (threads 0..63), its slot codes and lists (threads 80..127) and
-// header (threads 64, 65) into the context's buffers
+// a tile's operand rows of MMA 1 (threads 64..127), its header (threads 128, 129) and its slot
+// codes and lists (threads 160..207) into the context's buffers.  Warp 0, which issues the MMAs,
+// takes no part: while MMA 2 runs it loads the epilogue operands
 template <int NB, int K1, bool BF>
 __device__ __forceinline__ void stage_tile_inputs(const StageArgs& a, int64_t tile, int ct, __half* sA1, float2* sRow,
                                                   uint32_t* sCode, uint8_t* sList, int* sHdr) {
     const int64_t e0 = tile * ET;
     const int nel = (a.ne - e0) < (int64_t)ET ? (int)(a.ne - e0) : ET;
-    if (ct < 64) {
-        const int r = ct;
+    if (ct >= 64 && ct < 128) {
+        const int r = ct - 64;
         if (r < 5 * nel) {
             const int e = r / 5, v = r - 5 * e;
             sRow[r] = build_row<NB, K1, BF>(a.U_hi + ((e0 + e) * 5 + v) * NB, sA1, r, a.inv_beta1);
         } else {
             zero_row(sA1, r, K1);
         }
-    } else if (ct < 64 + THDR) {
-        sHdr[ct - 64] = __ldg(a.thdr + tile * THDR + (ct - 64));
-    } else if (ct >= 80 && ct < 80 + SLOTS) {
-        const int t2 = ct - 80;
+    } else if (ct >= 128 && ct < 128 + THDR) {
+        sHdr[ct - 128] = __ldg(a.thdr + tile * THDR + (ct - 128));
+    } else if (ct >= 160 && ct < 160 + SLOTS) {
+        const int t2 = ct - 160;
         const uint8_t* tl = a.tlist + tile * (2 * SLOTS);
         sCode[t2] = __ldg(a.slot + tile * SLOTS + t2);
         sList[t2] = __ldg(tl + t2);
@@ -370,8 +371,8 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         // the next tile: neighbour ids and cross count into sXn (loads issued here, stored after
         // this thread's traces), and an L2 prefetch of its contiguous blocks
         int xn0 = 0, xn1 = 0, xnc = 0;
-        if (ct >= CT - 32 && has_next) {
-            const int i = ct - (CT - 32);
+        if (ct >= 128 && ct < 160 && has_next) {
+            const int i = ct - 128;
             xn0 = __ldg(a.xnbr + nt * SLOTS + i);
             if (i + 32 < SLOTS) xn1 = __ldg(a.xnbr + nt * SLOTS + i + 32);
             if (i == 0) {
@@ -463,8 +464,8 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 for (int v = 0; v < 5; ++v) el[50 + v] = __int_as_float(rowpart(e * 5 + v, K2));
             }
         }
-        if (ct >= CT - 32 && has_next) {
-            const int i = ct - (CT - 32);
+        if (ct >= 128 && ct < 160 && has_next) {
+            const int i = ct - 128;
             sXn[i] = xn0;
             if (i + 32 < SLOTS) sXn[i + 32] = xn1;
             if (i == 0) sXn[SLOTS] = xnc;

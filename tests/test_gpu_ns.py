@@ -1,6 +1,9 @@
 """GPU parity of the Navier-Stokes residual (dg_ns_residual, FP64) with the oracle's viscous
 lines (oracle/ns.py): the whole residual at the FP64 bar of test_gpu_parity, and the viscous part
-alone (Navier-Stokes minus Euler residual, on both sides) to 1e-11 of its own largest value."""
+alone (Navier-Stokes minus Euler residual, on both sides) to 1e-11 of its own largest value; on
+periodic meshes, on a channel with no-slip walls and on the box channel (walls and far field).
+The result does not depend on the element order (bitwise), and a sampled full-size check runs
+on the 32^3 x 6 P2 mesh."""
 import math
 
 import numpy as np
@@ -27,6 +30,22 @@ def _state(P):
     return U
 
 
+def _case(kind, p, flux):
+    if kind == "periodic":
+        m = I.make_periodic_cube(3, jitter=0.15)
+        fs = None
+    elif kind == "channel":                    # no-slip walls at y = 0, 1; periodic in x, z
+        m = I.make_box_mesh((3, 3, 3), lengths=(1.5, 1.0, 1.2), periodic=(True, False, True), jitter=0.15)
+        fs = None
+    else:                                      # walls at y, z; far field at x
+        m = I.make_box_channel(4, 3, 3, jitter=0.15)
+        fs = I.freestream_state(0.3)
+    tag = None if all(m.periodic) else m.bc_tag
+    P = NSProblem(m.tet_vid, m.tet_xyz, tag, p=p, flux=flux, mu=MU, prandtl=PR, freestream=fs)
+    Pe = Problem(m.tet_vid, m.tet_xyz, tag, p=p, flux=flux, freestream=fs)
+    return m, P, Pe, fs
+
+
 def _gpu_ns(M, U, mu):
     torch = torch_cuda()
     Ud = torch.from_numpy(np.ascontiguousarray(U)).cuda()
@@ -36,21 +55,51 @@ def _gpu_ns(M, U, mu):
     return R.cpu().numpy()
 
 
+@pytest.mark.parametrize("kind", ["periodic", "channel", "box"])
 @pytest.mark.parametrize("p", [1, 2, 3])
 @pytest.mark.parametrize("flux", ["rusanov", "roe"])
-def test_ns_residual_matches_oracle(p, flux):
-    m = I.make_periodic_cube(3, jitter=0.15)
-    P = NSProblem(m.tet_vid, m.tet_xyz, None, p=p, flux=flux, mu=MU, prandtl=PR)
+def test_ns_residual_matches_oracle(kind, p, flux):
+    m, P, Pe, fs = _case(kind, p, flux)
     U = _state(P)
     ref = P.ns_residual(U)
-    ref_e = Problem(m.tet_vid, m.tet_xyz, None, p=p, flux=flux).residual(U)
-    M = make_mesh(m, p, flux, renumber=dg.DG_ORDER_MORTON)
+    ref_e = Pe.residual(U)
+    M = make_mesh(m, p, flux, renumber=dg.DG_ORDER_MORTON, freestream=fs)
     Rg = _gpu_ns(M, U, MU)
     assert max_rel_err(Rg, ref, term_scale=residual_term_scale(P, U)) < 1e-12
     dv_o = ref - ref_e
     dv_g = Rg - gpu_residual(M, U)
     assert np.abs(dv_o).max() > 1e-3
     assert np.abs(dv_g - dv_o).max() < 1e-11 * np.abs(dv_o).max()
+
+
+@pytest.mark.parametrize("kind", ["periodic", "box"])
+def test_ns_residual_independent_of_element_order(kind):
+    m, P, _, fs = _case(kind, 2, "roe")
+    U = _state(P)
+    out = [_gpu_ns(make_mesh(m, 2, "roe", renumber=r, freestream=fs), U, MU)
+           for r in (dg.DG_ORDER_MORTON, dg.DG_ORDER_RCM, dg.DG_ORDER_ASIS)]
+    np.testing.assert_array_equal(out[0], out[1])
+    np.testing.assert_array_equal(out[0], out[2])
+
+
+def test_ns_full_size_32cube_p2_sampled():
+    """The 32^3 x 6 = 196,608-tet P2 mesh (the adjoint workload's mesh, periodic): the viscous part
+    of 1500 sampled elements' residuals against the oracle, whose gradient is evaluated on the
+    samples and their face neighbours only."""
+    m = I.make_periodic_cube(32, jitter=0.10)
+    P = NSProblem(m.tet_vid, m.tet_xyz, None, p=2, flux="roe", mu=MU, prandtl=PR)
+    U = P.project(lambda x: I.isentropic_vortex(x), rule="volume")
+    U[:, 1:4] += 0.002 * np.random.default_rng(3).standard_normal(U[:, 1:4].shape)
+    rows = np.sort(np.random.default_rng(11).choice(m.ne, 1500, replace=False))
+    need = np.unique(np.concatenate([rows, P.nbr[rows].ravel()]))
+    Z = np.full((m.ne, 3, 5, P.nb), np.nan)
+    Z[need] = P.gradient(U, need)
+    ref_v = P._weak_rhs_ns(U, Z, rows) - P._weak_rhs(U, rows)
+    ref_v = np.linalg.solve(P.mass(rows), ref_v.transpose(0, 2, 1)).transpose(0, 2, 1)
+    M = make_mesh(m, 2, "roe", renumber=dg.DG_ORDER_MORTON)
+    dv_g = (_gpu_ns(M, U, MU) - gpu_residual(M, U))[rows]
+    assert np.abs(ref_v).max() > 1e-3
+    assert np.abs(dv_g - ref_v).max() < 1e-11 * np.abs(ref_v).max()
 
 
 def test_ns_residual_zero_viscosity_is_the_euler_residual():
@@ -61,15 +110,12 @@ def test_ns_residual_zero_viscosity_is_the_euler_residual():
     np.testing.assert_array_equal(_gpu_ns(M, U, 0.0), gpu_residual(M, U))
 
 
-def test_ns_residual_refuses_boundaries_and_other_precisions():
+def test_ns_residual_refuses_other_precisions():
     torch = torch_cuda()
-    box = I.make_box_channel(3, 2, 2, jitter=0.1)
-    Mb = dg.Mesh(box.tet_vid, box.tet_xyz, box.bc_tag, order=1, precision=dg.DG_FP64, flux=dg.DG_ROE,
-                 freestream=tuple(I.freestream_state(0.3)))
     m = I.make_periodic_cube(3, jitter=0.1)
-    Mf = make_mesh(m, 1, "roe", precision="fp32")
-    for M, ne in ((Mb, box.ne), (Mf, m.ne)):
-        U = torch.zeros((ne, 5, 4), dtype=torch.float64, device="cuda")
+    for prec in ("fp32", "mixed"):
+        M = make_mesh(m, 1, "roe", precision=prec)
+        U = torch.zeros((m.ne, 5, 4), dtype=torch.float64, device="cuda")
         R = torch.empty_like(U)
         with pytest.raises(dg.DGError) as e:
             dg.dg_ns_residual(M.handle, U, R, MU, PR)
