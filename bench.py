@@ -689,18 +689,40 @@ def run_study(args):
         ren = {"morton": dg.DG_ORDER_MORTON, "hilbert": dg.DG_ORDER_HILBERT, "rcm": dg.DG_ORDER_RCM,
                "asis": dg.DG_ORDER_ASIS}[order_of(args)]
         rows = []
-        for pname, prec in (("f64", dg.DG_FP64), ("f16x2-tc/f32/ff32", dg.DG_MIXED_FP16),
-                            ("bf16x2-tc/f32/ff32", dg.DG_MIXED_BF16)):
+        for pname, prec, cons in (("f64", dg.DG_FP64, False), ("f16x2-tc/f32/ff32", dg.DG_MIXED_FP16, False),
+                                  ("f16x2-tc/f32/ff32, conservative mode 0", dg.DG_MIXED_FP16, True),
+                                  ("bf16x2-tc/f32/ff32", dg.DG_MIXED_BF16, False),
+                                  ("bf16x2-tc/f32/ff32, conservative mode 0", dg.DG_MIXED_BF16, True)):
             nsteps = args.steps
             M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, tag, order=p, precision=prec, flux=fl, renumber=ren,
                         freestream=fs)
-            dg.dg_set_state(M.handle, M.project(field))
-            t0, _ = dg.dg_integrals(M.handle)
+            if cons:
+                dg.dg_set_conservative(M.handle, True)
+            U0 = M.project(field)
+            dg.dg_set_state(M.handle, U0)
             dt = dg.dg_stable_dt(M.handle, 0.1)
+            # stage time of this form (CUDA events over 5 steps after 2), then the drift run from U0
+            dg.dg_rk3_step(M.handle, dt, 2)
+            torch.cuda.synchronize()
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record()
+            dg.dg_rk3_step(M.handle, dt, 5)
+            eb.record()
+            torch.cuda.synchronize()
+            ms_step = ea.elapsed_time(eb) / 5
+            dg.dg_set_state(M.handle, U0)
+            t0, _ = dg.dg_integrals(M.handle)
             acc = np.zeros(5)
             t_start = time.perf_counter()
             for _ in range(nsteps):
-                if w["box"]:
+                if w["box"] and cons:
+                    # the boundary flux each stage applied: the totals move by -dt (B1/6 + B2/6 + 2 B3/3)
+                    B = []
+                    for st in (1, 2, 3):
+                        dg.dg_rk_stage(M.handle, st, dt)
+                        B.append(dg.dg_applied_boundary_flux(M.handle))
+                    acc += dt * (B[0] / 6.0 + B[1] / 6.0 + 2.0 * B[2] / 3.0)
+                elif w["box"]:
                     # B at the three stage states: the totals move by -dt (B0/6 + B1/6 + 2 B2/3)
                     b0 = dg.dg_boundary_flux(M.handle)
                     dg.dg_rk_stage(M.handle, 1, dt)
@@ -716,14 +738,17 @@ def run_study(args):
             M.close()
             d = t1 - t0 + acc
             rows.append({"precision": pname, "steps": nsteps, "dt": dt, "seconds": time.perf_counter() - t_start,
+                         "ms_per_step": ms_step,
                          "totals_start": t0.tolist(), "boundary_flux_integral": (-acc).tolist(),
                          "drift": d.tolist(),
                          "rel_drift_mass": abs(d[0]) / abs(t0[0]),
                          "rel_drift_momentum": float(np.linalg.norm(d[1:4]) / np.linalg.norm(t0[1:4])),
                          "rel_drift_energy": abs(d[4]) / abs(t0[4])})
         out.update({"rows": rows,
-                    "note": "drift = change of the totals + dt sum over steps of (B0/6 + B1/6 + 2 B2/3), B the "
-                            "boundary-flux integral at the stage states (0 on periodic meshes)"})
+                    "note": "drift = change of the totals + dt sum over steps of the boundary flux (0 on periodic "
+                            "meshes): B0/6 + B1/6 + 2 B2/3 at the stage states, re-evaluated in FP64 "
+                            "(dg_boundary_flux), or for the conservative mode the flux each stage applied "
+                            "(dg_applied_boundary_flux); ms_per_step from CUDA events over 5 steps"})
     else:
         rows = []
         for name, order in (("input (random)", dg.DG_ORDER_ASIS), ("RCM", dg.DG_ORDER_RCM),

@@ -178,6 +178,33 @@ dg_status dg_rk_stage(dg_mesh* mesh, int stage, double dt, void* stream);
 /* nsteps SSP-RK3 steps (3 stages each) on the internal state, in place. */
 dg_status dg_rk3_step(dg_mesh* mesh, double dt, int nsteps, void* stream);
 
+/* Conservative mode-0 update of the mixed-precision forms (enable 1) or the
+ * default (enable 0).  Discrete conservation (Eq. 11 with the constant test
+ * function: the volume line vanishes and every interior face's flux enters
+ * its two elements with opposite signs) holds in the mixed forms only to
+ * FP32 round-off, since the cell averages come out of the FP32-accumulated
+ * projection and a face to another tile is evaluated by each side from its
+ * own traces.  With this mode on, every stage also writes each (element,
+ * face)'s flux integral, and a second kernel computes the cell-average
+ * residual in FP64 as -(phi_0 / |det J|) sum_f 2|S_f| C_f, with one area per
+ * face and C_f the face's integral made antisymmetric between its two sides.
+ * The |det J|-weighted totals of the state then change only by the boundary
+ * fluxes, to FP64 round-off, and the other modes are unchanged.  Mixed meshes
+ * only (else DG_ERR_UNSUPPORTED); the first enable allocates 20 floats and 5
+ * doubles per element, owned by the mesh.  Applies to dg_residual,
+ * dg_rk_stage and dg_rk3_step; dg_partition_create refuses a mesh with the
+ * mode on. */
+dg_status dg_set_conservative(dg_mesh* mesh, int enable);
+
+/* The boundary-flux integral B_v = sum over boundary faces of 2|S_f| C_f,v
+ * that the last conservative-mode stage (or residual) applied: the totals of
+ * the state change by exactly -b dt B in that stage, to FP64 round-off (the
+ * bookkeeping of dg_boundary_flux, which re-evaluates the flux in FP64 from a
+ * state, agrees with it to the mixed forms' precision).  out receives 5
+ * doubles; zeros before the first stage.  DG_ERR_UNSUPPORTED unless the mesh
+ * is in the conservative mode.  Synchronises the stream. */
+dg_status dg_applied_boundary_flux(dg_mesh* mesh, double out[5], void* stream);
+
 /* dt = cfl * min_e h_e / ((2p+1)(|u|_e + c_e)), h_e = 3 vol_e / max face
  * area, from the element means of the internal state (Sec. III-C: local
  * steps, then a deterministic two-pass minimum).  Synchronises the stream. */

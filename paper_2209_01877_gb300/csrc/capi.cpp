@@ -74,6 +74,14 @@ void free_mesh(dg_mesh* m) {
     cudaFree(m->d_io);
     cudaFree(m->d_Z);
     cudaFree(m->d_HB);
+    cudaFree(m->d_hs);
+    cudaFree(m->d_wslot);
+    cudaFree(m->d_farea);
+    cudaFree(m->d_fown);
+    cudaFree(m->d_ncan);
+    cudaFree(m->d_flist);
+    cudaFree(m->d_T);
+    cudaFree(m->d_Hs);
     if (m->rk_exec) cudaGraphExecDestroy(m->rk_exec);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     cudaFree(m->d_red);
@@ -190,6 +198,12 @@ dg_status dg_mesh_create(const int32_t* tet_vid, const double* tet_xyz, const in
         DG_TRY(upload(&m->d_mlist, lists.data(), lists.size(), s));
         DG_TRY(upload(&m->d_mhdr, cnt.data(), cnt.size(), s));
         DG_TRY(upload(&m->d_mxnbr, xnbr.data(), xnbr.size(), s));
+    }
+    if (m->precision == DG_FP64) {
+        // every face's traces and flux once (owner flags, canonical normals, trace and flux buffers)
+        dg::build_face_owners(m->host, m->h_fown, m->h_ncan);
+        cudaError_t e = dg::setup_face_once(m, m->h_fown, m->h_ncan, m->host.ne, s);
+        if (e != cudaSuccess) { free_mesh(m); return cuda_fail(e, "face buffers"); }
     }
     if (m->precision == DG_FP64) {
         m->d_tab = m->d_tab64;   // shared; freed once below
@@ -390,6 +404,63 @@ dg_status dg_ns_residual(dg_mesh* m, const double* U, double* R, double mu, doub
     return DG_OK;
 }
 
+dg_status dg_set_conservative(dg_mesh* m, int enable) {
+    if (!m) return fail(DG_ERR_ARG, "mesh must be non-NULL");
+    if (!is_mixed(m)) return fail(DG_ERR_UNSUPPORTED, "the conservative mode-0 update is a mixed-precision option");
+    if (enable && !m->d_hs) {
+        const int64_t ne = m->host.ne;
+        // |det J| per element and 2|S_f| per face from the caller-order geometry (x0, J with the
+        // edges from vertex 0 as columns); the value of a face is computed once, from its
+        // lower-numbered element, and stored in both of its slots
+        std::vector<double> det(ne), area(4 * ne, 0.0);
+        auto edges = [&](int64_t e, double E[3][3]) {
+            const double* J = m->host.x0J.data() + (size_t)m->host.perm[e] * 12 + 3;
+            for (int k = 0; k < 3; ++k)
+                for (int d = 0; d < 3; ++d) E[k][d] = J[3 * d + k];
+        };
+        auto cross_norm = [](const double a[3], const double b[3]) {
+            const double c0 = a[1] * b[2] - a[2] * b[1], c1 = a[2] * b[0] - a[0] * b[2], c2 = a[0] * b[1] - a[1] * b[0];
+            return std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+        };
+        for (int64_t e = 0; e < ne; ++e) {
+            double E[3][3];
+            edges(e, E);
+            det[e] = std::fabs(E[0][0] * (E[1][1] * E[2][2] - E[1][2] * E[2][1]) -
+                               E[0][1] * (E[1][0] * E[2][2] - E[1][2] * E[2][0]) +
+                               E[0][2] * (E[1][0] * E[2][1] - E[1][1] * E[2][0]));
+            for (int f = 0; f < 4; ++f) {
+                const int32_t n = m->host.nbr[e * 4 + f];
+                if (n >= 0 && n < e) continue;   // the lower-numbered side computes the face
+                double a2;
+                if (f == 0) {
+                    const double u[3] = {E[1][0] - E[0][0], E[1][1] - E[0][1], E[1][2] - E[0][2]};
+                    const double w[3] = {E[2][0] - E[0][0], E[2][1] - E[0][1], E[2][2] - E[0][2]};
+                    a2 = cross_norm(u, w);
+                } else {
+                    const int k0 = f == 1 ? 1 : 0, k1 = f == 3 ? 1 : 2;   // the face's two edges from vertex 0
+                    a2 = cross_norm(E[k0], E[k1]);
+                }
+                area[e * 4 + f] = a2;
+                if (n >= 0) area[(int64_t)n * 4 + (m->host.fcode[e * 4 + f] & 3)] = a2;
+            }
+        }
+        // the mode-0 pass uses w = phi_0 A_f / |det J| per slot (no division on the device); the
+        // applied boundary flux uses A_f itself
+        const double phi0 = m->ref.tab[dg::TabLayout(m->p).phiq];
+        std::vector<double> wslot(4 * ne);
+        for (int64_t i = 0; i < 4 * ne; ++i) wslot[i] = phi0 * area[i] / det[i / 4];
+        DG_CUDA(cudaMalloc(&m->d_hs, (size_t)ne * 20 * sizeof(float)));
+        DG_CUDA(cudaMemset(m->d_hs, 0, (size_t)ne * 20 * sizeof(float)));
+        DG_CUDA(cudaMalloc(&m->d_wslot, (size_t)ne * 4 * sizeof(double)));
+        DG_CUDA(cudaMalloc(&m->d_farea, (size_t)ne * 4 * sizeof(double)));
+        DG_CUDA(cudaMemcpy(m->d_wslot, wslot.data(), wslot.size() * sizeof(double), cudaMemcpyHostToDevice));
+        DG_CUDA(cudaMemcpy(m->d_farea, area.data(), area.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    m->conservative = enable != 0;
+    m->rk_graph_dt = -1.0;   // a captured step graph holds the launches of the other mode
+    return DG_OK;
+}
+
 namespace {
 // one fused residual + RK stage: out = a U0 + b (U + dt R(U))
 cudaError_t stage_launch(dg_mesh* m, void* U, void* U0, void* out, double dt, double a, double b, cudaStream_t s) {
@@ -530,6 +601,22 @@ dg_status dg_boundary_flux(dg_mesh* m, const double* U, int stage, double out[5]
     }
     double* d_out = m->d_red + RED_SLOTS;
     DG_CUDA(dg::launch_boundary_flux(m, in, m->d_red, d_out, s));
+    DG_CUDA(cudaMemcpyAsync(m->h_red, d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    for (int v = 0; v < 5; ++v) out[v] = m->h_red[v];
+    return DG_OK;
+}
+
+dg_status dg_applied_boundary_flux(dg_mesh* m, double out[5], void* stream) {
+    if (!m || !out) return fail(DG_ERR_ARG, "mesh and out must be non-NULL");
+    if (!m->conservative) return fail(DG_ERR_UNSUPPORTED, "the mesh is not in the conservative mixed mode");
+    if (m->host.n_bfaces == 0) {
+        for (int v = 0; v < 5; ++v) out[v] = 0.0;
+        return DG_OK;
+    }
+    cudaStream_t s = as_stream(stream);
+    double* d_out = m->d_red + RED_SLOTS;
+    DG_CUDA(dg::launch_applied_boundary_flux(m, m->d_red, d_out, s));
     DG_CUDA(cudaMemcpyAsync(m->h_red, d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
     DG_CUDA(cudaStreamSynchronize(s));
     for (int v = 0; v < 5; ++v) out[v] = m->h_red[v];

@@ -51,6 +51,7 @@ struct ResArgs {
     Real dt, a, b;         // out = a*U0 + b*(U + dt*R) in RK mode
     Real gamma, roe_eps;
     Real finf[5];          // free-stream conserved state
+    const Real* Hs;        // face-once path: per (element, face, point) the face flux, outward
     unsigned int* status;  // device status word
 };
 

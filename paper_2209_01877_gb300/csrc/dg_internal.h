@@ -43,6 +43,7 @@ struct MeshHost {
 
 bool build_mesh(const int32_t* tet_vid, const double* tet_xyz, const int8_t* bc_tag, int64_t ne,
                 int renumber, MeshHost& out, int& code, std::string& err);
+void build_face_owners(const MeshHost& h, std::vector<uint8_t>& fown, std::vector<double>& ncan);
 
 }  // namespace dg
 
@@ -83,6 +84,26 @@ struct dg_mesh {
     unsigned int* d_status = nullptr;
     double* d_Z = nullptr;         // Navier-Stokes auxiliary gradient [ne][3][5][Nb] (lazy)
     double* d_HB = nullptr;        // Navier-Stokes own viscous face fluxes [ne][4][Nqf][4] (lazy)
+    // mixed precision, conservative mode-0 update (dg_set_conservative): per (element, face) flux
+    // integrals [ne][4][5]; per slot the weight phi_0 2|S_f| / |det J| of the mode-0 pass and the
+    // face's 2|S_f| (one value per face, in both slots)
+    bool conservative = false;
+    float* d_hs = nullptr;
+    double* d_wslot = nullptr;
+    double* d_farea = nullptr;
+    // one evaluation per face (FP64): per slot the owner flag and the owner's outward normal
+    // (host copies kept for partitions), the list of slots whose face flux this mesh evaluates,
+    // the number of elements with traces (own + halo on a partition's mesh), and the trace and
+    // face-flux buffers [n_trace][4][Nqf][5] (lazy)
+    bool face_once = false;
+    std::vector<uint8_t> h_fown;
+    std::vector<double> h_ncan;
+    uint8_t* d_fown = nullptr;
+    void* d_ncan = nullptr;        // Real [ne][4][3]
+    int32_t* d_flist = nullptr;
+    int64_t n_flist = 0, n_trace = 0;
+    void* d_T = nullptr;
+    void* d_Hs = nullptr;
     // small meshes: a CUDA graph of several captured RK3 steps at one dt (dg_rk3_step)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t rk_exec = nullptr;
@@ -94,6 +115,10 @@ struct dg_mesh {
 namespace dg {
 cudaError_t launch_residual(dg_mesh* m, const void* U, const void* U0, void* out, int mode,
                             double dt, double a, double b, cudaStream_t s);
+// the face-once path's device data from per-slot owner flags and normals of the mesh's own
+// elements (n_trace - ne halo elements follow them in the state)
+cudaError_t setup_face_once(dg_mesh* m, const std::vector<uint8_t>& fown, const std::vector<double>& ncan,
+                            int64_t n_trace, cudaStream_t s);
 cudaError_t launch_gather(dg_mesh* m, const double* user, void* internal, cudaStream_t s);   // caller -> internal
 // Navier-Stokes lines (FP64, no boundary faces): the BR1 gradient into Z, then the viscous
 // volume and face terms added to the residual R (internal order)
@@ -105,6 +130,7 @@ cudaError_t launch_scatter_f32(dg_mesh* m, const float* internal, double* user, 
 cudaError_t launch_stable_dt(dg_mesh* m, const void* U, double* d_out, cudaStream_t s);
 cudaError_t launch_integrals(dg_mesh* m, const void* U, double* d_out6, cudaStream_t s);
 cudaError_t launch_boundary_flux(dg_mesh* m, const void* U, double* d_partial, double* d_out5, cudaStream_t s);
+cudaError_t launch_applied_boundary_flux(dg_mesh* m, double* d_partial, double* d_out5, cudaStream_t s);
 cudaError_t launch_project(dg_mesh* m, const double* f, double* U, cudaStream_t s);
 cudaError_t launch_volume_points(dg_mesh* m, const double* d_x0J, double* xyz, cudaStream_t s);
 cudaError_t launch_residual_vjp(dg_mesh* m, const void* U, const void* lam, const void* X, const void* Y,

@@ -318,4 +318,30 @@ bool build_mesh(const int32_t* tet_vid, const double* tet_xyz, const int8_t* bc_
     return true;
 }
 
+// Owners and canonical normals of the faces (the one-evaluation-per-face FP64/FP32 path).  A
+// boundary face belongs to its element; an interior face to the element with the smaller caller
+// index, so the choice, like every other input of the face flux, does not depend on the
+// internal element order.  ncan holds the owner's outward unit normal -grad lambda_f /
+// |grad lambda_f| (from the owner's J^-1) in both slots of the face.
+void build_face_owners(const MeshHost& h, std::vector<uint8_t>& fown, std::vector<double>& ncan) {
+    const int64_t ne = h.ne;
+    fown.assign((size_t)4 * ne, 0);
+    ncan.assign((size_t)12 * ne, 0.0);
+    for (int64_t e = 0; e < ne; ++e)
+        for (int f = 0; f < 4; ++f) {
+            const int32_t n = h.nbr[4 * e + f];
+            if (n >= 0 && h.perm[n] < h.perm[e]) continue;
+            fown[4 * e + f] = 1;
+            const double* I = h.jinv.data() + 9 * e;
+            double g[3];
+            for (int d = 0; d < 3; ++d) g[d] = f == 0 ? -(I[d] + I[3 + d] + I[6 + d]) : I[3 * (f - 1) + d];
+            const double gn = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            for (int d = 0; d < 3; ++d) {
+                const double nd = -g[d] / gn;
+                ncan[12 * e + 3 * f + d] = nd;
+                if (n >= 0) ncan[12 * (int64_t)n + 3 * (h.fcode[4 * e + f] & 3) + d] = nd;
+            }
+        }
+}
+
 }  // namespace dg

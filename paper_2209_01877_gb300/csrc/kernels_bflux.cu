@@ -77,6 +77,28 @@ __global__ void __launch_bounds__(BT) k_bflux_local(const Real* __restrict__ U, 
     if (threadIdx.x < 5) block_sum[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
 }
 
+// the conservative mixed mode's own boundary flux: per boundary slot 4 e + f, the face's 2|S_f|
+// times the flux integral the last stage used (one value per face, as in the mode-0 update)
+__global__ void __launch_bounds__(BT) k_applied_bflux_local(const float* __restrict__ hs,
+                                                            const double* __restrict__ farea,
+                                                            const int32_t* __restrict__ bface, int64_t nbf,
+                                                            double* __restrict__ block_sum) {
+    __shared__ double red[5][BT];
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int64_t i = blockIdx.x * (int64_t)BT + threadIdx.x; i < nbf; i += (int64_t)gridDim.x * BT) {
+        const int64_t sl = bface[i];
+        for (int v = 0; v < 5; ++v) acc[v] += farea[sl] * (double)hs[sl * 5 + v];
+    }
+    for (int v = 0; v < 5; ++v) red[v][threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int s = BT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int v = 0; v < 5; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) block_sum[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
+}
+
 __global__ void __launch_bounds__(BT) k_bflux_final(const double* __restrict__ in, int nblk, double* __restrict__ out) {
     __shared__ double red[5][BT];
     double acc[5] = {0, 0, 0, 0, 0};
@@ -113,6 +135,15 @@ cudaError_t launch_boundary_flux(dg_mesh* m, const void* U, double* d_partial, d
                                                  m->d_jinv64, m->d_tab64, m->d_bface, m->d_nbr, nbf, m->nb, m->nqf,
                                                  L.phif, off_fw, m->flux, m->gamma, m->roe_eps, fi[0], fi[1], fi[2],
                                                  fi[3], fi[4], d_partial);
+    k_bflux_final<<<1, BT, 0, s>>>(d_partial, nblk, d_out5);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_applied_boundary_flux(dg_mesh* m, double* d_partial, double* d_out5, cudaStream_t s) {
+    const int64_t nbf = m->host.n_bfaces;
+    int nblk = (int)std::min<int64_t>((nbf + BT - 1) / BT, MAX_BLOCKS);
+    if (nblk < 1) nblk = 1;
+    k_applied_bflux_local<<<nblk, BT, 0, s>>>(m->d_hs, m->d_farea, m->d_bface, nbf, d_partial);
     k_bflux_final<<<1, BT, 0, s>>>(d_partial, nblk, d_out5);
     return cudaGetLastError();
 }

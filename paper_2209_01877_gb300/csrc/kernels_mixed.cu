@@ -175,6 +175,11 @@ struct StageArgs {
     float inv_beta1, inv_beta2;
     float finf[5];
     unsigned int* status;
+    // conservative mode-0 update (null when off): per (element, local face) the outward flux
+    // integral sum_q wf_q H_q [ne][4][5], read back from the projection operand; the RK update
+    // then leaves the residual out of mode 0, which k_cons_mode0 adds from these integrals
+    float* hs;
+    float wf[16];           // face quadrature weights (sum 1/2)
 };
 
 using namespace mx;
@@ -262,7 +267,7 @@ __device__ __forceinline__ void issue_staged_blocks(const StageArgs& a, const in
     tc::cp_async_commit();
 }
 
-template <int P, int FLUX, bool BF>
+template <int P, int FLUX, bool BF, bool CONS>
 __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     using S = SPlan<P>;
     constexpr int NB = S::NB, NQ = S::NQ, NQF = S::NQF, NQF4 = S::NQF4, FPAD = S::FPAD;
@@ -613,6 +618,36 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         // the next tile's operand rows and metadata (A1, the rows, codes and lists are free: MMA 1
         // and the flux phase are done)
         if (has_next) stage_tile_inputs<NB, K1, BF>(a, nt, ct, sA1, sRow, sCode, sList, sHdr);
+        // conservative mode: each (element, face, variable)'s flux integral from the split pairs
+        // of the projection operand (read-only, like MMA 2): A2 = sc (H - Fbar.n), so
+        // sum_q wf_q H_q = (sum_q wf_q A2_q + fb W) / sc with W = sum_q wf_q
+        if (CONS && ct >= 32) {
+            for (int i = ct - 32; i < 20 * nel; i += CT - 32) {
+                const int sl = i / 5, v = i - 5 * sl, e = sl >> 2, f = sl & 3;
+                const uint32_t* row = reinterpret_cast<const uint32_t*>(sA2);
+                const int rp = __float_as_int(sEl[e * ELW + 50 + v]) >> 1;
+                float acc = 0.f, W = 0.f;
+#pragma unroll
+                for (int q = 0; q < NQF; ++q) {
+                    const uint32_t w = row[(kpart(3 * NQ + f * NQF + q) >> 1) + rp];
+                    float hi, lo;
+                    if constexpr (BF) {
+                        const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&w);
+                        hi = __low2float(b);
+                        lo = __high2float(b);
+                    } else {
+                        const __half2 b = *reinterpret_cast<const __half2*>(&w);
+                        hi = __low2float(b);
+                        lo = __high2float(b);
+                    }
+                    acc = fmaf(a.wf[q], hi + lo, acc);
+                    W += a.wf[q];
+                }
+                const float4 r0 = sRec[3 * sl], r1 = sRec[3 * sl + 1], r2 = sRec[3 * sl + 2];
+                const float fb = v == 0 ? r1.x : v == 1 ? r1.y : v == 2 ? r1.z : v == 3 ? r1.w : r2.x;
+                a.hs[(e0 * 4 + sl) * 5 + v] = __fdividef(fmaf(fb, W, acc), r0.w);
+            }
+        }
         // epilogue operands in flight while the tensor cores work.  This thread holds rows rA, rB
         // (16-lane layout) and, per column group g of its part, the mode pair (or single mode) below:
         //   part 0: modes cb, cb+1 (columns 0..7);
@@ -689,9 +724,12 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 const int64_t g = rr == 0 ? gA : gB;
                 const float inv = sEl[(r / 5) * ELW + 49];
                 const float2 R = mul2(dp[rr], f2(inv));
+                // conservative mode: mode 0 is k_cons_mode0's, in FP64 (left unwritten here)
+                const bool skip0 = CONS && j0 == 0;
                 const float Rs = ds[rr] * inv;
                 if (a.mode == 0) {
-                    if (pair_in) *reinterpret_cast<float2*>(a.out_hi + g + j0) = R;
+                    if (pair_in && skip0) a.out_hi[g + j0 + 1] = R.y;
+                    else if (pair_in) *reinterpret_cast<float2*>(a.out_hi + g + j0) = R;
                     if (one_in) a.out_hi[g + j1] = Rs;
                     continue;
                 }
@@ -705,8 +743,14 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                     const float2 bb = sub2(sm, uh);
                     const float2 err = add2(add2(sub2(uh, sub2(sm, bb)), sub2(dlt, bb)), ul);
                     const float2 oh = add2(sm, err);
-                    *reinterpret_cast<float2*>(a.out_hi + g + j0) = oh;
-                    *reinterpret_cast<float2*>(a.out_lo + g + j0) = sub2(err, sub2(oh, sm));
+                    const float2 ol = sub2(err, sub2(oh, sm));
+                    if (skip0) {
+                        a.out_hi[g + j0 + 1] = oh.y;
+                        a.out_lo[g + j0 + 1] = ol.y;
+                    } else {
+                        *reinterpret_cast<float2*>(a.out_hi + g + j0) = oh;
+                        *reinterpret_cast<float2*>(a.out_lo + g + j0) = ol;
+                    }
                 }
                 if (one_in) {
                     const float uh = u[rr][0][2], ul = u[rr][1][2];
@@ -741,10 +785,10 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
 
 namespace {
 
-template <int P, int FLUX, bool BF>
-cudaError_t slaunch(const StageArgs& sa, cudaStream_t s, int nsm) {
+template <int P, int FLUX, bool BF, bool CONS>
+cudaError_t slaunch1(const StageArgs& sa, cudaStream_t s, int nsm) {
     using S = SPlan<P>;
-    auto k = k_stage_mixed<P, FLUX, BF>;
+    auto k = k_stage_mixed<P, FLUX, BF, CONS>;
     static bool init = false;
     if (!init) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::BYTES);
@@ -754,6 +798,13 @@ cudaError_t slaunch(const StageArgs& sa, cudaStream_t s, int nsm) {
     const int64_t ntiles = (sa.ne + ET - 1) / ET;
     k<<<(int)std::min<int64_t>((ntiles + 1) / 2, (int64_t)nsm), MT, S::BYTES, s>>>(sa);
     return cudaGetLastError();
+}
+
+// the conservative mode's stage kernel is a separate instantiation, so that the default one
+// carries none of its code
+template <int P, int FLUX, bool BF>
+cudaError_t slaunch(const StageArgs& sa, cudaStream_t s, int nsm) {
+    return sa.hs ? slaunch1<P, FLUX, BF, true>(sa, s, nsm) : slaunch1<P, FLUX, BF, false>(sa, s, nsm);
 }
 
 }  // namespace
@@ -902,6 +953,74 @@ void build_mixed_tiles(const MeshHost& h, std::vector<uint32_t>& slot, std::vect
     }
 }
 
+namespace {
+
+// Conservative mode-0 residual (FP64): R_0 = -sum_f w_f C_f, w_f = phi_0 A_f / |det J| (Eq. 11's
+// face line with the constant test function; the volume line vanishes for it).  A_f = 2 |S_f| is
+// one value per face (computed once on the host and given to both sides) and C_f the face's flux
+// integral made antisymmetric: (own - neighbour's) / 2 on interior faces (a difference of two
+// floats, exact in FP64), the own value on boundary faces.  Both sides of a face therefore add
+// exactly opposite amounts of A_f C_f, and the |det J|-weighted sum of the mode-0 updates over the
+// mesh cancels to FP64 round-off.  RK mode forms the whole mode-0 update U + a (U0 - U) + b dt R_0
+// in FP64 from the float-float planes (the stage kernel leaves mode 0 unwritten: the stage
+// increment rounded in FP32 would not be conservative) and stores it as a float-float pair;
+// residual mode writes R_0.  Thread per element.
+struct ConsArgs {
+    const float* hs;        // [ne][4][5]
+    const int32_t* nbr;     // [ne][4]
+    const uint8_t* fcode;   // [ne][4]
+    const double* wslot;    // [ne][4] phi_0 2 |S_f| / |det J|
+    const float* U_hi;      // state planes (RK mode)
+    const float* U_lo;
+    const float* U0_hi;     // RK base state (stages 2, 3; null in stage 1)
+    const float* U0_lo;
+    float* out_hi;
+    float* out_lo;
+    int64_t ne;
+    int nb, mode;
+    double a, bdt;
+};
+
+__global__ void __launch_bounds__(256) k_cons_mode0(ConsArgs c) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= c.ne) return;
+    double R0[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const float* own = c.hs + (e * 4 + f) * 5;
+        const int32_t n = c.nbr[e * 4 + f];
+        const double w = c.wslot[e * 4 + f];
+        if (n >= 0) {
+            const float* oth = c.hs + ((int64_t)n * 4 + (c.fcode[e * 4 + f] & 3)) * 5;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) R0[v] -= w * (0.5 * ((double)own[v] - (double)oth[v]));
+        } else {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) R0[v] -= w * (double)own[v];
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        const int64_t k = (e * 5 + v) * c.nb;
+        if (c.mode == 0) {
+            c.out_hi[k] = (float)R0[v];
+            continue;
+        }
+        // float-float planes hold <= 48 bits, so hi + lo is exact in FP64
+        const double u = (double)c.U_hi[k] + (double)c.U_lo[k];
+        double x = u;
+        if (c.U0_hi) x += c.a * (((double)c.U0_hi[k] + (double)c.U0_lo[k]) - u);
+        x += c.bdt * R0[v];
+        const float h = (float)x;
+        c.out_hi[k] = h;
+        c.out_lo[k] = (float)(x - (double)h);
+    }
+}
+
+}  // namespace
+
+static cudaError_t stage_dispatch(dg_mesh* m, const StageArgs& r, cudaStream_t s, int nsm);
+
 cudaError_t launch_residual_mixed(dg_mesh* m, const float* U_hi, const float* U_lo, const float* U0_hi,
                                   const float* U0_lo, float* out_hi, float* out_lo, int mode, double dt, double ca,
                                   double cb, cudaStream_t s) {
@@ -931,10 +1050,41 @@ cudaError_t launch_residual_mixed(dg_mesh* m, const float* U_hi, const float* U_
     r.inv_beta2 = m->mix_inv_b2;
     for (int v = 0; v < 5; ++v) r.finf[v] = (float)m->finf[v];
     r.status = m->d_status;
+    r.hs = m->conservative ? m->d_hs : nullptr;
+    for (int q = 0; q < 16; ++q) r.wf[q] = 0.f;
+    if (r.hs) {
+        // the face rule of the mesh's own reference data (meshes of partitions carry none and
+        // never run in this mode)
+        if ((int)m->ref.face_w.size() < m->nqf || m->nqf > 16) return cudaErrorInvalidValue;
+        for (int q = 0; q < m->nqf; ++q) r.wf[q] = (float)m->ref.face_w[q];
+    }
     if (mode != 0 && std::fabs(ca + cb - 1.0) > 1e-12) return cudaErrorInvalidValue;
     int nsm = 0;
     cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
     if (e != cudaSuccess) return e;
+    e = stage_dispatch(m, r, s, nsm);
+    if (e != cudaSuccess || !r.hs) return e;
+    ConsArgs c;
+    c.hs = m->d_hs;
+    c.nbr = m->d_nbr;
+    c.fcode = m->d_fcode;
+    c.wslot = m->d_wslot;
+    c.U_hi = U_hi;
+    c.U_lo = U_lo;
+    c.U0_hi = ca != 0.0 ? U0_hi : nullptr;
+    c.U0_lo = U0_lo;
+    c.out_hi = out_hi;
+    c.out_lo = out_lo;
+    c.ne = m->host.ne;
+    c.nb = m->nb;
+    c.mode = mode;
+    c.a = ca;
+    c.bdt = cb * dt;
+    k_cons_mode0<<<(unsigned)((m->host.ne + 255) / 256), 256, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
+static cudaError_t stage_dispatch(dg_mesh* m, const StageArgs& r, cudaStream_t s, int nsm) {
     const bool roe = m->flux == DG_ROE;
     if (m->precision == DG_MIXED_BF16) {
         switch (m->p) {

@@ -155,6 +155,11 @@ void free_sub(dg_mesh* s) {
     cudaFree(s->d_jinv);
     cudaFree(s->d_jinv64);
     cudaFree(s->d_red);
+    cudaFree(s->d_fown);
+    cudaFree(s->d_ncan);
+    cudaFree(s->d_flist);
+    cudaFree(s->d_T);
+    cudaFree(s->d_Hs);
     delete s;
 }
 
@@ -196,6 +201,7 @@ extern "C" {
 dg_status dg_partition_create(dg_mesh* m, int k, void* stream, dg_partition** out) {
     if (!m || !out) return pfail(DG_ERR_ARG, "mesh and out must be non-NULL");
     *out = nullptr;
+    if (m->conservative) return pfail(DG_ERR_UNSUPPORTED, "partitions evaluate the default mode-0 update");
     dg_partition* P = new dg_partition();
     P->parent = m;
     P->k = k;
@@ -250,6 +256,15 @@ dg_status dg_partition_create(dg_mesh* m, int k, void* stream, dg_partition** ou
             PTRY(upload_vec(&sm->d_mlist, lists, s));
             PTRY(upload_vec(&sm->d_mhdr, hdr, s));
             PTRY(upload_vec(&sm->d_mxnbr, xnbr, s));
+        }
+        // face-once form: the parent's owner flags and normals of the own slots; the faces shared
+        // with halo elements are evaluated here too, in their owner's orientation, so every own
+        // element receives the flux the whole mesh would give it
+        if (m->face_once) {
+            const int64_t c = pl.count;
+            std::vector<uint8_t> fo(m->h_fown.begin() + 4 * pl.first, m->h_fown.begin() + 4 * (pl.first + c));
+            std::vector<double> nc(m->h_ncan.begin() + 12 * pl.first, m->h_ncan.begin() + 12 * (pl.first + c));
+            PTRY(dg::setup_face_once(sm, fo, nc, c + (int64_t)pl.halo.size(), s));
         }
         // local state: own then halo blocks (mixed: hi plane of own + halo, then the lo plane)
         const size_t nloc = (size_t)(pl.count + pl.halo.size()) * nv_of(m);

@@ -28,7 +28,8 @@ EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_element_ord
             "dg_rk_stage", "dg_rk3_step", "dg_stable_dt", "dg_integrals", "dg_residual_vjp", "dg_rk3_step_vjp",
             "dg_kinetic_energy_grad", "dg_sync_status", "dg_reference_data", "dg_conserved_totals_noalloc",
             "dg_boundary_flux", "dg_partition_plan", "dg_partition_create", "dg_partition_destroy",
-            "dg_partition_info", "dg_partition_residual", "dg_partition_reductions",
+            "dg_partition_info", "dg_partition_residual", "dg_partition_reductions", "dg_set_conservative",
+            "dg_applied_boundary_flux",
             "dg_last_error"]
 
 
@@ -70,6 +71,8 @@ def load():
             "dg_ns_residual": [vp, vp, vp, C.c_double, C.c_double, vp],
             "dg_rk_stage": [vp, C.c_int, C.c_double, vp],
             "dg_rk3_step": [vp, C.c_double, C.c_int, vp],
+            "dg_set_conservative": [vp, C.c_int],
+            "dg_applied_boundary_flux": [vp, C.POINTER(C.c_double), vp],
             "dg_stable_dt": [vp, C.c_double, C.POINTER(C.c_double), vp],
             "dg_integrals": [vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double), vp],
             "dg_boundary_flux": [vp, vp, C.c_int, C.POINTER(C.c_double), vp],
@@ -236,6 +239,18 @@ def dg_rk_stage(mesh, stage, dt, stream=None):
 
 def dg_rk3_step(mesh, dt, nsteps=1, stream=None):
     _check(load().dg_rk3_step(mesh, float(dt), int(nsteps), _stream(stream)))
+
+
+def dg_set_conservative(mesh, enable=True):
+    """Mixed meshes: the conservative mode-0 update on (True) or off."""
+    _check(load().dg_set_conservative(mesh, 1 if enable else 0))
+
+
+def dg_applied_boundary_flux(mesh, stream=None):
+    """Conservative mixed mode: the boundary-flux integral the last stage applied (5 values)."""
+    out = (C.c_double * 5)()
+    _check(load().dg_applied_boundary_flux(mesh, out, _stream(stream)))
+    return np.array(list(out))
 
 
 def dg_stable_dt(mesh, cfl, stream=None):
