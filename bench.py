@@ -636,8 +636,13 @@ def run_study(args):
         R = torch.empty_like(U)
         n = max(args.steps, 3)
         res = {}
+        dg.dg_set_state(M.handle, U)
+        dt_ns = 0.1 * dg.dg_stable_dt(M.handle, 0.1)
         calls = (("dg_residual (Euler)", lambda: dg.dg_residual(M.handle, U, R)),
-                 ("dg_ns_residual (mu 1e-3, Pr 0.72)", lambda: dg.dg_ns_residual(M.handle, U, R, 1e-3, 0.72)))
+                 ("dg_ns_residual (mu 1e-3, Pr 0.72)", lambda: dg.dg_ns_residual(M.handle, U, R, 1e-3, 0.72)),
+                 ("dg_rk3_step (Euler, one step)", lambda: dg.dg_rk3_step(M.handle, dt_ns, 1)),
+                 ("dg_ns_rk3_step (one step, mu 1e-3, Pr 0.72)",
+                  lambda: dg.dg_ns_rk3_step(M.handle, dt_ns, 1, 1e-3, 0.72)))
         for name, call in calls:
             call()
             torch.cuda.synchronize()
@@ -648,7 +653,8 @@ def run_study(args):
             b.record()
             torch.cuda.synchronize()
             t = a.elapsed_time(b) / 1e3 / n
-            res[name] = {"ms": t * 1e3, "dof_updates_per_s": mesh.ne * 5 * NB[p] / t}
+            stages = 3 if "step" in name else 1          # one RK3 step = three residual evaluations
+            res[name] = {"ms": t * 1e3, "dof_updates_per_s": stages * mesh.ne * 5 * NB[p] / t}
         dg.dg_sync_status(M.handle)
         M.close()
         out.update({"precision": "f64", "tets": mesh.ne, "calls": n, "rows": res})

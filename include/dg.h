@@ -170,6 +170,14 @@ dg_status dg_residual(dg_mesh* mesh, const double* U, double* R, void* stream);
  * per element), both owned by the mesh. */
 dg_status dg_ns_residual(dg_mesh* mesh, const double* U, double* R, double mu, double prandtl, void* stream);
 
+/* nsteps SSP-RK3 steps of the Navier-Stokes equations on the internal state, in
+ * place: each stage evaluates the residual of dg_ns_residual (Euler lines, then
+ * the viscous lines) and applies the stage update of dg_rk_stage.  FP64 meshes
+ * only (else DG_ERR_UNSUPPORTED); mu and prandtl as for dg_ns_residual; mu = 0
+ * gives the Euler stages (as three kernels per stage instead of one).  Uses the
+ * residual work buffer, so a dg_residual call between steps is safe. */
+dg_status dg_ns_rk3_step(dg_mesh* mesh, double dt, int nsteps, double mu, double prandtl, void* stream);
+
 /* One SSP-RK3 stage on the internal state, fused with the residual (one
  * kernel launch): stage 1 U1 = U0 + dt R(U0); stage 2 U2 = 3/4 U0 + 1/4 (U1
  * + dt R(U1)); stage 3 U0 <- 1/3 U0 + 2/3 (U2 + dt R(U2)). */

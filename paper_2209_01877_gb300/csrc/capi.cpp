@@ -550,6 +550,36 @@ dg_status dg_rk3_step(dg_mesh* m, double dt, int nsteps, void* stream) {
     return DG_OK;
 }
 
+dg_status dg_ns_rk3_step(dg_mesh* m, double dt, int nsteps, double mu, double prandtl, void* stream) {
+    if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
+    if (nsteps < 0) return fail(DG_ERR_ARG, "nsteps must be >= 0");
+    if (!(mu >= 0.0) || !(prandtl > 0.0)) return fail(DG_ERR_ARG, "mu must be >= 0 and prandtl > 0");
+    if (m->precision != DG_FP64) return fail(DG_ERR_UNSUPPORTED, "the Navier-Stokes step runs on FP64 meshes");
+    if (nsteps == 0) return DG_OK;
+    if (!m->has_state) return fail(DG_ERR_NOSTATE, "no state set");
+    if (!(dt >= 0.0)) return fail(DG_ERR_ARG, "dt must be >= 0");
+    dg_status st = ensure_work_buffers(m);
+    if (st != DG_OK) return st;
+    if (mu > 0.0) {
+        if (!m->d_Z) DG_CUDA(cudaMalloc(&m->d_Z, (size_t)m->host.ne * 15 * m->nb * sizeof(double)));
+        if (!m->d_HB) DG_CUDA(cudaMalloc(&m->d_HB, dg::ns_face_buffer_doubles(m->p, m->host.ne) * sizeof(double)));
+    }
+    cudaStream_t s = as_stream(stream);
+    const int64_t n = m->host.ne * 5 * m->nb;
+    double** B = reinterpret_cast<double**>(m->d_B);
+    double* R = static_cast<double*>(m->d_W[1]);
+    // the stages of dg_rk_stage, each as residual (Euler + viscous lines) then update
+    const struct { int in, base, out; double a, b; } stages[3] = {{0, -1, 1, 0.0, 1.0}, {1, 0, 2, 0.75, 0.25},
+                                                                  {2, 0, 0, 1.0 / 3.0, 2.0 / 3.0}};
+    for (int k = 0; k < nsteps; ++k)
+        for (const auto& g : stages) {
+            DG_CUDA(dg::launch_residual(m, B[g.in], nullptr, R, 0, 0.0, 0.0, 0.0, s));
+            if (mu > 0.0) DG_CUDA(dg::launch_ns_viscous(m, B[g.in], m->d_Z, m->d_HB, R, mu, prandtl, s));
+            DG_CUDA(dg::launch_rk_axpy(B[g.in], g.base >= 0 ? B[g.base] : nullptr, R, B[g.out], n, dt, g.a, g.b, s));
+        }
+    return DG_OK;
+}
+
 dg_status dg_stable_dt(dg_mesh* m, double cfl, double* dt_host, void* stream) {
     if (!m || !dt_host) return fail(DG_ERR_ARG, "mesh and dt_host must be non-NULL");
     if (!m->has_state) return fail(DG_ERR_NOSTATE, "no state set");

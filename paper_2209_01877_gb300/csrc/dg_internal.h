@@ -125,6 +125,9 @@ cudaError_t launch_gather(dg_mesh* m, const double* user, void* internal, cudaSt
 cudaError_t launch_ns_viscous(dg_mesh* m, const double* U, double* Z, double* HB, double* R, double mu,
                               double prandtl, cudaStream_t s);
 size_t ns_face_buffer_doubles(int p, int64_t ne);
+// FP64 SSP-RK3 stage from a stored residual: out = a U0 + b (U + dt R)
+cudaError_t launch_rk_axpy(const double* U, const double* U0, const double* R, double* out, int64_t n, double dt,
+                           double a, double b, cudaStream_t s);
 cudaError_t launch_scatter(dg_mesh* m, const void* internal, double* user, cudaStream_t s);  // internal -> caller
 cudaError_t launch_scatter_f32(dg_mesh* m, const float* internal, double* user, cudaStream_t s);
 cudaError_t launch_stable_dt(dg_mesh* m, const void* U, double* d_out, cudaStream_t s);

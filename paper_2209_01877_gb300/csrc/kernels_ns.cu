@@ -457,6 +457,26 @@ cudaError_t ns_launch(const NSArgs& args, cudaStream_t s, int nsm) {
 
 size_t ns_face_buffer_doubles(int p, int64_t ne) { return (size_t)ne * 4 * nqf_of(p) * 4; }
 
+namespace {
+// SSP-RK3 stage update from a stored residual: out = a U0 + b (U + dt R) (a = 0: U0 unread)
+__global__ void __launch_bounds__(256) k_rk_axpy(const double* __restrict__ U, const double* __restrict__ U0,
+                                                 const double* __restrict__ R, double* out, int64_t n, double dt,
+                                                 double a, double b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double r = b * (U[i] + dt * R[i]);
+        if (a != 0.0) r += a * U0[i];
+        out[i] = r;
+    }
+}
+}  // namespace
+
+cudaError_t launch_rk_axpy(const double* U, const double* U0, const double* R, double* out, int64_t n, double dt,
+                           double a, double b, cudaStream_t s) {
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+    k_rk_axpy<<<(unsigned)blocks, 256, 0, s>>>(U, U0, R, out, n, dt, a, b);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ns_viscous(dg_mesh* m, const double* U, double* Z, double* HB, double* R, double mu,
                               double prandtl, cudaStream_t s) {
     NSArgs a;

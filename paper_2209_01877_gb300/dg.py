@@ -28,7 +28,7 @@ EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_element_ord
             "dg_rk_stage", "dg_rk3_step", "dg_stable_dt", "dg_integrals", "dg_residual_vjp", "dg_rk3_step_vjp",
             "dg_kinetic_energy_grad", "dg_sync_status", "dg_reference_data", "dg_conserved_totals_noalloc",
             "dg_boundary_flux", "dg_partition_plan", "dg_partition_create", "dg_partition_destroy",
-            "dg_partition_info", "dg_partition_residual", "dg_partition_reductions", "dg_set_conservative",
+            "dg_partition_info", "dg_partition_residual", "dg_partition_reductions", "dg_set_conservative", "dg_ns_rk3_step",
             "dg_applied_boundary_flux",
             "dg_last_error"]
 
@@ -72,6 +72,7 @@ def load():
             "dg_rk_stage": [vp, C.c_int, C.c_double, vp],
             "dg_rk3_step": [vp, C.c_double, C.c_int, vp],
             "dg_set_conservative": [vp, C.c_int],
+            "dg_ns_rk3_step": [vp, C.c_double, C.c_int, C.c_double, C.c_double, vp],
             "dg_applied_boundary_flux": [vp, C.POINTER(C.c_double), vp],
             "dg_stable_dt": [vp, C.c_double, C.POINTER(C.c_double), vp],
             "dg_integrals": [vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double), vp],
@@ -239,6 +240,10 @@ def dg_rk_stage(mesh, stage, dt, stream=None):
 
 def dg_rk3_step(mesh, dt, nsteps=1, stream=None):
     _check(load().dg_rk3_step(mesh, float(dt), int(nsteps), _stream(stream)))
+
+
+def dg_ns_rk3_step(mesh, dt, nsteps, mu, prandtl=0.72, stream=None):
+    _check(load().dg_ns_rk3_step(mesh, float(dt), int(nsteps), float(mu), float(prandtl), _stream(stream)))
 
 
 def dg_set_conservative(mesh, enable=True):
