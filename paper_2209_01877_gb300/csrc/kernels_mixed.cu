@@ -958,8 +958,8 @@ namespace {
 // Conservative mode-0 residual (FP64): R_0 = -sum_f w_f C_f, w_f = phi_0 A_f / |det J| (Eq. 11's
 // face line with the constant test function; the volume line vanishes for it).  A_f = 2 |S_f| is
 // one value per face (computed once on the host and given to both sides) and C_f the face's flux
-// integral made antisymmetric: (own - neighbour's) / 2 on interior faces (a difference of two
-// floats, exact in FP64), the own value on boundary faces.  Both sides of a face therefore add
+// integral made antisymmetric: (own - neighbour's) / 2 on interior faces (a rounded difference,
+// exactly the negative of the other side's), the own value on boundary faces.  Both sides of a face therefore add
 // exactly opposite amounts of A_f C_f, and the |det J|-weighted sum of the mode-0 updates over the
 // mesh cancels to FP64 round-off.  RK mode forms the whole mode-0 update U + a (U0 - U) + b dt R_0
 // in FP64 from the float-float planes (the stage kernel leaves mode 0 unwritten: the stage
@@ -991,9 +991,11 @@ __global__ void __launch_bounds__(256) k_cons_mode0(ConsArgs c) {
         const int32_t n = c.nbr[e * 4 + f];
         const double w = c.wslot[e * 4 + f];
         if (n >= 0) {
+            // (own - other's) / 2 in FP32: a rounded difference is exactly antisymmetric, so the
+            // two sides still add exact negatives
             const float* oth = c.hs + ((int64_t)n * 4 + (c.fcode[e * 4 + f] & 3)) * 5;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) R0[v] -= w * (0.5 * ((double)own[v] - (double)oth[v]));
+            for (int v = 0; v < 5; ++v) R0[v] -= w * (double)(0.5f * (own[v] - oth[v]));
         } else {
 #pragma unroll
             for (int v = 0; v < 5; ++v) R0[v] -= w * (double)own[v];
