@@ -109,6 +109,12 @@ def test_conservative_refusals():
     with pytest.raises(dg.DGError) as e:
         dg.dg_partition_create(Mc.handle, 2)
     assert e.value.status == 7
+    # the applied boundary flux exists only in the conservative mode
+    Md = _mesh(m, 2, conservative=False)
+    with pytest.raises(dg.DGError) as e:
+        dg.dg_applied_boundary_flux(Md.handle)
+    assert e.value.status == 7
+    np.testing.assert_array_equal(dg.dg_applied_boundary_flux(Mc.handle), np.zeros(5))   # periodic
 
 
 def test_conservative_box_totals_follow_the_applied_boundary_flux():
