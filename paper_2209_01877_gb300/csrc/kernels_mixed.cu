@@ -33,19 +33,22 @@
 // written to both sides.  Only faces to other tiles read the neighbour's
 // coefficients (from L2: consecutive elements of a space-filling-curve or RCM
 // order are spatial neighbours); their traces are evaluated on the CUDA cores
-// in FP32 while the tensor cores work.  Per tile:
-//   build    operand rows of the own coefficients (modes 1..); the
-//            neighbours' coefficient blocks were copied by cp.async while
-//            the previous tile's MMA 2 ran;
-//   MMA 1    own values at the 4 Nqf face points and the Nq volume points;
-//            meanwhile the neighbours' traces (FP32) and the per-element
-//            scaled J^-1 and mean-state fluxes;
+// in FP32 while the tensor cores work.  Per tile (the next tile's inputs are
+// prepared inside this tile's phases, so no phase waits on their loads):
+//   MMA 1    own values at the 4 Nqf face points and the Nq volume points, from
+//            operand rows built during the previous tile's MMA 2; meanwhile the
+//            neighbours' traces (FP32), the per-element scaled J^-1 and
+//            mean-state fluxes, and the next tile's neighbour ids and L2
+//            prefetch;
 //   stage    TMEM -> shared memory (FP32 point states; 16-lane TMEM loads so
-//            all 32 lanes of a warp work on the M = 64 accumulator);
+//            all 32 lanes of a warp work on the M = 64 accumulator); the next
+//            tile's neighbour blocks are requested by cp.async;
 //   flux     volume points: contravariant flux deviation; face points:
 //            Rusanov / Roe flux (ghost state on boundary faces) written to
 //            the owner's and, for in-tile faces, the partner's operand;
 //   MMA 2    projection onto the weighted basis gradients and face lift;
+//            meanwhile the epilogue's operands are loaded and the next tile's
+//            operand rows, slot codes and lists are built;
 //   epilogue R, or the RK stage in float-float, straight to global memory.
 // Every wait on the tensor cores is bounded; on time-out the context sets a
 // status bit and leaves its tile loop (all its threads together); the CTA
