@@ -285,12 +285,13 @@ def test_library_projection_matches_oracle_volume_rule():
         np.testing.assert_allclose(M.project(f), P.project(f, rule="volume"), atol=1e-13, rtol=0)
 
 
-def test_nonphysical_state_is_reported():
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+def test_nonphysical_state_is_reported(precision):
     m = I.make_periodic_cube(3, jitter=0.15)
     P = Problem(m.tet_vid, m.tet_xyz, None, p=1)
     U = P.project(I.uniform_flow)
     U[7, 0, :] *= -1.0                       # negative density in one element
-    M = make_mesh(m, 1)
+    M = make_mesh(m, 1, precision=precision)
     torch = torch_cuda()
     Ud = torch.from_numpy(U).cuda()
     R = torch.empty_like(Ud)
