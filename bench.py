@@ -631,7 +631,9 @@ def run_study(args):
         out.update({"stable_dt_ms_incl_sync": t_dt * 1e3, "integrals_ms_incl_sync": t_int * 1e3,
                     "tets": mesh.ne})
     elif args.study == "ns":
-        M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, tag, order=p, precision=dg.DG_FP64, flux=fl, freestream=fs)
+        prec = {"fp32": dg.DG_FP32, "mixed": dg.DG_MIXED_FP16, "mixed-bf16": dg.DG_MIXED_BF16}.get(args.precision,
+                                                                                                  dg.DG_FP64)
+        M = dg.Mesh(mesh.tet_vid, mesh.tet_xyz, tag, order=p, precision=prec, flux=fl, freestream=fs)
         U = torch.from_numpy(M.project(field)).cuda()
         R = torch.empty_like(U)
         n = max(args.steps, 3)
@@ -657,7 +659,9 @@ def run_study(args):
             res[name] = {"ms": t * 1e3, "dof_updates_per_s": stages * mesh.ne * 5 * NB[p] / t}
         dg.dg_sync_status(M.handle)
         M.close()
-        out.update({"precision": "f64", "tets": mesh.ne, "calls": n, "rows": res})
+        out.update({"precision": {dg.DG_FP64: "f64", dg.DG_FP32: "f32", dg.DG_MIXED_FP16: "f16x2-tc/f32/ff32",
+                                  dg.DG_MIXED_BF16: "bf16x2-tc/f32/ff32"}[prec], "tets": mesh.ne, "calls": n,
+                    "rows": res})
     elif args.study == "launch":
         prec = {"fp64": dg.DG_FP64, "fp32": dg.DG_FP32, "mixed-bf16": dg.DG_MIXED_BF16}.get(args.precision,
                                                                                          dg.DG_MIXED_FP16)

@@ -164,18 +164,23 @@ dg_status dg_residual(dg_mesh* mesh, const double* U, double* R, void* stream);
  * viscous flux is F_v(wall state, interior gradient) . n with no energy flux)
  * and keeps the Euler wall flux; a DG_BC_FARFIELD face takes the interior
  * trace and the interior viscous flux.  U and R as for dg_residual (device,
- * caller order; U NULL = the internal state).  FP64 meshes only (else
- * DG_ERR_UNSUPPORTED).  The first call with mu > 0 allocates the gradient
- * buffer (15 Nb doubles per element) and a face-flux buffer (16 Nqf doubles
- * per element), both owned by the mesh. */
+ * caller order; U NULL = the internal state).  Arithmetic of the mesh's
+ * precision: FP64 meshes in FP64; FP32 meshes in FP32; the mixed forms take
+ * their Euler lines from the tensor-core kernel and the viscous lines in FP32
+ * from the state's leading FP32 plane.  The first call with mu > 0 allocates
+ * the gradient buffer (15 Nb values per element) and a face-flux buffer
+ * (16 Nqf values per element), in that arithmetic, owned by the mesh. */
 dg_status dg_ns_residual(dg_mesh* mesh, const double* U, double* R, double mu, double prandtl, void* stream);
 
 /* nsteps SSP-RK3 steps of the Navier-Stokes equations on the internal state, in
  * place: each stage evaluates the residual of dg_ns_residual (Euler lines, then
- * the viscous lines) and applies the stage update of dg_rk_stage.  FP64 meshes
- * only (else DG_ERR_UNSUPPORTED); mu and prandtl as for dg_ns_residual; mu = 0
- * gives the Euler stages (as three kernels per stage instead of one).  Uses the
- * residual work buffer, so a dg_residual call between steps is safe. */
+ * the viscous lines) and applies the stage update of dg_rk_stage in the mesh's
+ * state format (the mixed forms: the FP32 increment added to the float-float
+ * state without rounding error).  mu and prandtl as for dg_ns_residual; mu = 0
+ * gives the Euler stages (as separate kernels instead of one fused stage).
+ * DG_ERR_UNSUPPORTED on a mesh in the conservative mode (dg_set_conservative
+ * applies to the Euler stages).  Uses the residual work buffer, so a
+ * dg_residual call between steps is safe. */
 dg_status dg_ns_rk3_step(dg_mesh* mesh, double dt, int nsteps, double mu, double prandtl, void* stream);
 
 /* One SSP-RK3 stage on the internal state, fused with the residual (one

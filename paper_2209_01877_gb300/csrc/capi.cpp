@@ -380,10 +380,27 @@ dg_status dg_residual(dg_mesh* m, const double* U, double* R, void* stream) {
     return DG_OK;
 }
 
+namespace {
+// the Euler residual of an internal-order state into R (the mesh's precision; the mixed forms
+// write FP32 R) and the Navier-Stokes buffers (element size of the viscous passes' arithmetic)
+cudaError_t euler_residual_internal(dg_mesh* m, const void* in, void* R, cudaStream_t s) {
+    if (is_mixed(m))
+        return dg::launch_residual_mixed(m, static_cast<const float*>(in), nullptr, nullptr, nullptr,
+                                         static_cast<float*>(R), nullptr, 0, 0.0, 0.0, 0.0, s);
+    return dg::launch_residual(m, in, nullptr, R, 0, 0.0, 0.0, 0.0, s);
+}
+
+dg_status ensure_ns_buffers(dg_mesh* m) {
+    const size_t rs = m->precision == DG_FP64 ? sizeof(double) : sizeof(float);
+    if (!m->d_Z) DG_CUDA(cudaMalloc(&m->d_Z, (size_t)m->host.ne * 15 * m->nb * rs));
+    if (!m->d_HB) DG_CUDA(cudaMalloc(&m->d_HB, dg::ns_face_buffer_values(m->p, m->host.ne) * rs));
+    return DG_OK;
+}
+}  // namespace
+
 dg_status dg_ns_residual(dg_mesh* m, const double* U, double* R, double mu, double prandtl, void* stream) {
     if (!m || !R) return fail(DG_ERR_ARG, "mesh and R must be non-NULL");
     if (!(mu >= 0.0) || !(prandtl > 0.0)) return fail(DG_ERR_ARG, "mu must be >= 0 and prandtl > 0");
-    if (m->precision != DG_FP64) return fail(DG_ERR_UNSUPPORTED, "the Navier-Stokes residual runs on FP64 meshes");
     if (!U && !m->has_state) return fail(DG_ERR_NOSTATE, "no state set and U is NULL");
     dg_status st = ensure_work_buffers(m);
     if (st != DG_OK) return st;
@@ -393,14 +410,14 @@ dg_status dg_ns_residual(dg_mesh* m, const double* U, double* R, double mu, doub
         DG_CUDA(dg::launch_gather(m, U, m->d_W[0], s));
         in = m->d_W[0];
     }
-    DG_CUDA(dg::launch_residual(m, in, nullptr, m->d_W[1], 0, 0.0, 0.0, 0.0, s));
+    DG_CUDA(euler_residual_internal(m, in, m->d_W[1], s));
     if (mu > 0.0) {
-        if (!m->d_Z) DG_CUDA(cudaMalloc(&m->d_Z, (size_t)m->host.ne * 15 * m->nb * sizeof(double)));
-        if (!m->d_HB) DG_CUDA(cudaMalloc(&m->d_HB, dg::ns_face_buffer_doubles(m->p, m->host.ne) * sizeof(double)));
-        DG_CUDA(dg::launch_ns_viscous(m, static_cast<const double*>(in), m->d_Z, m->d_HB,
-                                      static_cast<double*>(m->d_W[1]), mu, prandtl, s));
+        st = ensure_ns_buffers(m);
+        if (st != DG_OK) return st;
+        DG_CUDA(dg::launch_ns_viscous(m, in, m->d_Z, m->d_HB, m->d_W[1], mu, prandtl, s));
     }
-    DG_CUDA(dg::launch_scatter(m, m->d_W[1], R, s));
+    if (is_mixed(m)) DG_CUDA(dg::launch_scatter_f32(m, static_cast<const float*>(m->d_W[1]), R, s));
+    else DG_CUDA(dg::launch_scatter(m, m->d_W[1], R, s));
     return DG_OK;
 }
 
@@ -554,28 +571,28 @@ dg_status dg_ns_rk3_step(dg_mesh* m, double dt, int nsteps, double mu, double pr
     if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
     if (nsteps < 0) return fail(DG_ERR_ARG, "nsteps must be >= 0");
     if (!(mu >= 0.0) || !(prandtl > 0.0)) return fail(DG_ERR_ARG, "mu must be >= 0 and prandtl > 0");
-    if (m->precision != DG_FP64) return fail(DG_ERR_UNSUPPORTED, "the Navier-Stokes step runs on FP64 meshes");
+    if (m->conservative)
+        return fail(DG_ERR_UNSUPPORTED, "the conservative mode-0 update applies to the Euler stages only");
     if (nsteps == 0) return DG_OK;
     if (!m->has_state) return fail(DG_ERR_NOSTATE, "no state set");
     if (!(dt >= 0.0)) return fail(DG_ERR_ARG, "dt must be >= 0");
     dg_status st = ensure_work_buffers(m);
     if (st != DG_OK) return st;
     if (mu > 0.0) {
-        if (!m->d_Z) DG_CUDA(cudaMalloc(&m->d_Z, (size_t)m->host.ne * 15 * m->nb * sizeof(double)));
-        if (!m->d_HB) DG_CUDA(cudaMalloc(&m->d_HB, dg::ns_face_buffer_doubles(m->p, m->host.ne) * sizeof(double)));
+        st = ensure_ns_buffers(m);
+        if (st != DG_OK) return st;
     }
     cudaStream_t s = as_stream(stream);
-    const int64_t n = m->host.ne * 5 * m->nb;
-    double** B = reinterpret_cast<double**>(m->d_B);
-    double* R = static_cast<double*>(m->d_W[1]);
+    void** B = m->d_B;
+    void* R = m->d_W[1];
     // the stages of dg_rk_stage, each as residual (Euler + viscous lines) then update
     const struct { int in, base, out; double a, b; } stages[3] = {{0, -1, 1, 0.0, 1.0}, {1, 0, 2, 0.75, 0.25},
                                                                   {2, 0, 0, 1.0 / 3.0, 2.0 / 3.0}};
     for (int k = 0; k < nsteps; ++k)
         for (const auto& g : stages) {
-            DG_CUDA(dg::launch_residual(m, B[g.in], nullptr, R, 0, 0.0, 0.0, 0.0, s));
+            DG_CUDA(euler_residual_internal(m, B[g.in], R, s));
             if (mu > 0.0) DG_CUDA(dg::launch_ns_viscous(m, B[g.in], m->d_Z, m->d_HB, R, mu, prandtl, s));
-            DG_CUDA(dg::launch_rk_axpy(B[g.in], g.base >= 0 ? B[g.base] : nullptr, R, B[g.out], n, dt, g.a, g.b, s));
+            DG_CUDA(dg::launch_rk_axpy(m, B[g.in], g.base >= 0 ? B[g.base] : nullptr, R, B[g.out], dt, g.a, g.b, s));
         }
     return DG_OK;
 }

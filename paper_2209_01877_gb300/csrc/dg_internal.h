@@ -120,14 +120,17 @@ cudaError_t launch_residual(dg_mesh* m, const void* U, const void* U0, void* out
 cudaError_t setup_face_once(dg_mesh* m, const std::vector<uint8_t>& fown, const std::vector<double>& ncan,
                             int64_t n_trace, cudaStream_t s);
 cudaError_t launch_gather(dg_mesh* m, const double* user, void* internal, cudaStream_t s);   // caller -> internal
-// Navier-Stokes lines (FP64, no boundary faces): the BR1 gradient into Z, then the viscous
-// volume and face terms added to the residual R (internal order)
-cudaError_t launch_ns_viscous(dg_mesh* m, const double* U, double* Z, double* HB, double* R, double mu,
-                              double prandtl, cudaStream_t s);
-size_t ns_face_buffer_doubles(int p, int64_t ne);
-// FP64 SSP-RK3 stage from a stored residual: out = a U0 + b (U + dt R)
-cudaError_t launch_rk_axpy(const double* U, const double* U0, const double* R, double* out, int64_t n, double dt,
-                           double a, double b, cudaStream_t s);
+// Navier-Stokes lines: the BR1 gradient into Z, then the viscous volume and face terms added to
+// the residual R (internal order), in the mesh's arithmetic (FP64 meshes FP64; FP32 and mixed
+// meshes FP32, U the state's hi plane); Z holds 15 Nb and HB ns_face_buffer_values values per
+// element of that type
+cudaError_t launch_ns_viscous(dg_mesh* m, const void* U, void* Z, void* HB, void* R, double mu, double prandtl,
+                              cudaStream_t s);
+size_t ns_face_buffer_values(int p, int64_t ne);
+// SSP-RK3 stage from a stored residual, out = a U0 + b (U + dt R), in the mesh's state format (the
+// mixed forms: float-float planes, FP32 residual)
+cudaError_t launch_rk_axpy(dg_mesh* m, const void* U, const void* U0, const void* R, void* out, double dt, double a,
+                           double b, cudaStream_t s);
 cudaError_t launch_scatter(dg_mesh* m, const void* internal, double* user, cudaStream_t s);  // internal -> caller
 cudaError_t launch_scatter_f32(dg_mesh* m, const float* internal, double* user, cudaStream_t s);
 cudaError_t launch_stable_dt(dg_mesh* m, const void* U, double* d_out, cudaStream_t s);

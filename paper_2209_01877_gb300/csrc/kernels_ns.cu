@@ -46,7 +46,7 @@ template <> struct NSTile<1> { static constexpr int EPB = 32; };
 template <> struct NSTile<2> { static constexpr int EPB = 16; };
 template <> struct NSTile<3> { static constexpr int EPB = 8; };
 
-// shared-memory plan (doubles) of the three kernels for order P
+// shared-memory plan (Reals) of the three kernels for order P
 template <int P>
 struct NSPlan {
     static constexpr int NB = nb_of(P), NQ = nq_of(P), NQF = nqf_of(P), EPB = NSTile<P>::EPB;
@@ -63,35 +63,38 @@ struct NSPlan {
     // lift pass: the face-lift table, -s Fn_nbr / 2
     static constexpr int L_REALS = 4 * NQF * NB + EPB * 4 * 4 * NQF + EPB * 4;
     static constexpr size_t ints = EPB * 4 * sizeof(int) + EPB * 4 + 6 * NQF + 16;
-    static constexpr size_t G_BYTES = G_REALS * sizeof(double) + ints;
-    static constexpr size_t V_BYTES = V_REALS * sizeof(double) + ints;
-    static constexpr size_t L_BYTES = L_REALS * sizeof(double) + ints;
+    // shared-memory bytes for an element size rs (8 FP64, 4 FP32)
+    static constexpr size_t g_bytes(size_t rs) { return G_REALS * rs + ints; }
+    static constexpr size_t v_bytes(size_t rs) { return V_REALS * rs + ints; }
+    static constexpr size_t l_bytes(size_t rs) { return L_REALS * rs + ints; }
 };
 
+template <typename Real>
 struct NSArgs {
-    const double* U;        // [ne][5][Nb] internal order
-    double* Z;              // [ne][3][5][Nb]
-    double* R;              // [ne][5][Nb] Euler residual, the viscous terms are added
-    double* HB;             // [ne][4][Nqf][4] own F_v . n at interior face points
+    const Real* U;        // [ne][5][Nb] internal order
+    Real* Z;              // [ne][3][5][Nb]
+    Real* R;              // [ne][5][Nb] Euler residual, the viscous terms are added
+    Real* HB;             // [ne][4][Nqf][4] own F_v . n at interior face points
     const int32_t* nbr;     // [ne][4] (boundary faces: -1 - bc type)
     const uint8_t* fcode;   // [ne][4]
-    const double* jinv;     // [ne][9]
-    const double* tab;      // basis tables (TabLayout)
+    const Real* jinv;     // [ne][9]
+    const Real* tab;      // basis tables (TabLayout)
     const int8_t* fperm;    // [6][Nqf]
     int64_t ne;
-    double mu, kappa, gamma;
+    Real mu, kappa, gamma;
 };
 
 // outward unit normals and s = |grad lambda_f| of the tile's faces from the row-major J^-1
-__device__ __forceinline__ void tile_geometry(const double* ji, int nel, int tid, double* geo) {
+template <typename Real>
+__device__ __forceinline__ void tile_geometry(const Real* ji, int nel, int tid, Real* geo) {
     for (int i = tid; i < nel * 4; i += NS_T) {
-        const double* I = ji + (i >> 2) * 9;
+        const Real* I = ji + (i >> 2) * 9;
         const int f = i & 3;
-        double g[3];
+        Real g[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) g[d] = f == 0 ? -(I[d] + I[3 + d] + I[6 + d]) : I[3 * (f - 1) + d];
-        const double s = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-        const double inv = -1.0 / s;
+        const Real s = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        const Real inv = Real(-1) / s;
         geo[4 * i + 0] = g[0] * inv;
         geo[4 * i + 1] = g[1] * inv;
         geo[4 * i + 2] = g[2] * inv;
@@ -100,30 +103,31 @@ __device__ __forceinline__ void tile_geometry(const double* ji, int nel, int tid
 }
 
 // F_v[d][v] from the state U[5] and its gradient Z[d][v]
-__device__ __forceinline__ void viscous_flux(const double U[5], const double Z[3][5], double mu, double kappa,
-                                             double gamma, double F[3][5]) {
-    const double ri = 1.0 / U[0];
-    const double u[3] = {U[1] * ri, U[2] * ri, U[3] * ri};
-    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const double T = (gamma - 1.0) * (U[4] - 0.5 * U[0] * uu) * ri;
-    double du[3][3], dT[3];   // du[i][d] = d u_i / d x_d
+template <typename Real>
+__device__ __forceinline__ void viscous_flux(const Real U[5], const Real Z[3][5], Real mu, Real kappa,
+                                             Real gamma, Real F[3][5]) {
+    const Real ri = Real(1) / U[0];
+    const Real u[3] = {U[1] * ri, U[2] * ri, U[3] * ri};
+    const Real uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const Real T = (gamma - Real(1)) * (U[4] - Real(0.5) * U[0] * uu) * ri;
+    Real du[3][3], dT[3];   // du[i][d] = d u_i / d x_d
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const double dr = Z[d][0];
+        const Real dr = Z[d][0];
 #pragma unroll
         for (int i = 0; i < 3; ++i) du[i][d] = (Z[d][1 + i] - u[i] * dr) * ri;
-        const double dp = (gamma - 1.0) * (Z[d][4] - (u[0] * Z[d][1] + u[1] * Z[d][2] + u[2] * Z[d][3]) + 0.5 * uu * dr);
+        const Real dp = (gamma - Real(1)) * (Z[d][4] - (u[0] * Z[d][1] + u[1] * Z[d][2] + u[2] * Z[d][3]) + Real(0.5) * uu * dr);
         dT[d] = (dp - T * dr) * ri;
     }
-    const double div = du[0][0] + du[1][1] + du[2][2];
+    const Real div = du[0][0] + du[1][1] + du[2][2];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        F[d][0] = 0.0;
-        double w = 0.0;
+        F[d][0] = Real(0);
+        Real w = Real(0);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            double t = mu * (du[i][d] + du[d][i]);
-            if (i == d) t -= (2.0 / 3.0) * mu * div;
+            Real t = mu * (du[i][d] + du[d][i]);
+            if (i == d) t -= Real(2.0 / 3.0) * mu * div;
             F[d][1 + i] = t;
             w += u[i] * t;
         }
@@ -132,36 +136,37 @@ __device__ __forceinline__ void viscous_flux(const double U[5], const double Z[3
 }
 
 // the no-slip adiabatic wall state: interior density and internal energy, at rest
-__device__ __forceinline__ void wall_state(const double U[5], double Q[5]) {
+template <typename Real>
+__device__ __forceinline__ void wall_state(const Real U[5], Real Q[5]) {
     Q[0] = U[0];
-    Q[1] = Q[2] = Q[3] = 0.0;
-    Q[4] = U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0];
+    Q[1] = Q[2] = Q[3] = Real(0);
+    Q[4] = U[4] - Real(0.5) * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0];
 }
 
 // values at one point of nf fields whose coefficient rows (NB each) start at c, basis values
 // phi[j * stride]
-template <int NB, int NF>
-__device__ __forceinline__ void point_fields(const double* c, const double* phi, int stride, double* out) {
+template <typename Real, int NB, int NF>
+__device__ __forceinline__ void point_fields(const Real* c, const Real* phi, int stride, Real* out) {
 #pragma unroll
     for (int v = 0; v < NF; ++v) {
-        double s = 0.0;
+        Real s = Real(0);
 #pragma unroll
         for (int j = 0; j < NB; ++j) s += c[v * NB + j] * phi[j * stride];
         out[v] = s;
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(NS_T) k_ns_grad(NSArgs a) {
+template <typename Real, int P>
+__global__ void __launch_bounds__(NS_T) k_ns_grad(NSArgs<Real> a) {
     using S = NSPlan<P>;
     constexpr int NB = S::NB, NQ = S::NQ, NQF = S::NQF, EPB = S::EPB;
     extern __shared__ __align__(16) unsigned char smem[];
-    double* tab = reinterpret_cast<double*>(smem);
-    double* cown = tab + S::TAB;
-    double* big = cown + S::G_OWN;
-    double* hq = big + S::G_NBR;
-    double* geo = hq + S::G_QH;
-    double* ji = geo + S::GEO;
+    Real* tab = reinterpret_cast<Real*>(smem);
+    Real* cown = tab + S::TAB;
+    Real* big = cown + S::G_OWN;
+    Real* hq = big + S::G_NBR;
+    Real* geo = hq + S::G_QH;
+    Real* ji = geo + S::GEO;
     int* snbr = reinterpret_cast<int*>(ji + S::JI);
     uint8_t* sfc = reinterpret_cast<uint8_t*>(snbr + EPB * 4);
     int8_t* sperm = reinterpret_cast<int8_t*>(sfc + EPB * 4);
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(NS_T) k_ns_grad(NSArgs a) {
         for (int i = tid; i < nel * 4 * 5 * NB; i += NS_T) {
             const int ef = i / (5 * NB), k = i - ef * 5 * NB;
             const int n = snbr[ef];
-            big[i] = n >= 0 ? a.U[(int64_t)n * 5 * NB + k] : 0.0;
+            big[i] = n >= 0 ? a.U[(int64_t)n * 5 * NB + k] : Real(0);
         }
         tile_geometry(ji, nel, tid, geo);
         __syncthreads();
@@ -192,23 +197,23 @@ __global__ void __launch_bounds__(NS_T) k_ns_grad(NSArgs a) {
         for (int i = tid; i < nel * 4 * NQF; i += NS_T) {
             const int ef = i / NQF, q = i - ef * NQF;
             const int el = ef >> 2, f = ef & 3;
-            double Um[5], Qh[5];
-            point_fields<NB, 5>(cown + el * 5 * NB, tab + S::PHIF + f * NB * NQF + q, NQF, Um);
+            Real Um[5], Qh[5];
+            point_fields<Real, NB, 5>(cown + el * 5 * NB, tab + S::PHIF + f * NB * NQF + q, NQF, Um);
             const int n = snbr[ef];
             if (n >= 0) {
                 const int code = sfc[ef];
                 const int fn = code & 3, qn = sperm[(code >> 2) * NQF + q];
-                double Up[5];
-                point_fields<NB, 5>(big + ef * 5 * NB, tab + S::PHIF + fn * NB * NQF + qn, NQF, Up);
+                Real Up[5];
+                point_fields<Real, NB, 5>(big + ef * 5 * NB, tab + S::PHIF + fn * NB * NQF + qn, NQF, Up);
 #pragma unroll
-                for (int v = 0; v < 5; ++v) Qh[v] = 0.5 * (Um[v] + Up[v]);
+                for (int v = 0; v < 5; ++v) Qh[v] = Real(0.5) * (Um[v] + Up[v]);
             } else if (n == -1 - DG_BC_WALL) {
                 wall_state(Um, Qh);
             } else {
 #pragma unroll
                 for (int v = 0; v < 5; ++v) Qh[v] = Um[v];
             }
-            const double s = geo[4 * ef + 3];
+            const Real s = geo[4 * ef + 3];
 #pragma unroll
             for (int v = 0; v < 5; ++v) hq[(ef * 5 + v) * NQF + q] = s * Qh[v];
         }
@@ -216,8 +221,8 @@ __global__ void __launch_bounds__(NS_T) k_ns_grad(NSArgs a) {
         // volume: Q at every (element, point), over the neighbour blocks
         for (int i = tid; i < nel * NQ; i += NS_T) {
             const int el = i / NQ, q = i - el * NQ;
-            double Uq[5];
-            point_fields<NB, 5>(cown + el * 5 * NB, tab + S::PHIQ + q, NQ, Uq);
+            Real Uq[5];
+            point_fields<Real, NB, 5>(cown + el * 5 * NB, tab + S::PHIQ + q, NQ, Uq);
 #pragma unroll
             for (int v = 0; v < 5; ++v) big[(el * 5 + v) * NQ + q] = Uq[v];
         }
@@ -226,26 +231,26 @@ __global__ void __launch_bounds__(NS_T) k_ns_grad(NSArgs a) {
         for (int i = tid; i < nel * 5 * NB; i += NS_T) {
             const int ev = i / NB, j = i - ev * NB;
             const int el = ev / 5, v = ev - el * 5;
-            double t[3];
-            const double* uq = big + ev * NQ;
+            Real t[3];
+            const Real* uq = big + ev * NQ;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                double s = 0.0;
+                Real s = Real(0);
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) s += uq[q] * tab[S::DPHIW + (k * NQ + q) * NB + j];
                 t[k] = s;
             }
-            const double* I = ji + el * 9;
-            double z[3];
+            const Real* I = ji + el * 9;
+            Real z[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) z[d] = -(I[d] * t[0] + I[3 + d] * t[1] + I[6 + d] * t[2]);
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-                const double* h = hq + ((el * 4 + f) * 5 + v) * NQF;
-                double s = 0.0;
+                const Real* h = hq + ((el * 4 + f) * 5 + v) * NQF;
+                Real s = Real(0);
 #pragma unroll
                 for (int q = 0; q < NQF; ++q) s += h[q] * tab[S::PHIFW + (f * NQF + q) * NB + j];
-                const double* nr = geo + 4 * (el * 4 + f);
+                const Real* nr = geo + 4 * (el * 4 + f);
 #pragma unroll
                 for (int d = 0; d < 3; ++d) z[d] += nr[d] * s;
             }
@@ -256,20 +261,20 @@ __global__ void __launch_bounds__(NS_T) k_ns_grad(NSArgs a) {
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(NS_T) k_ns_visc(NSArgs a) {
+template <typename Real, int P>
+__global__ void __launch_bounds__(NS_T) k_ns_visc(NSArgs<Real> a) {
     using S = NSPlan<P>;
     constexpr int NB = S::NB, NQ = S::NQ, NQF = S::NQF, EPB = S::EPB;
     extern __shared__ __align__(16) unsigned char smem[];
-    double* tab = reinterpret_cast<double*>(smem);
-    double* cuz = tab + S::TAB;          // [EPB][20][NB]: U (5 rows), then Z (15 rows, d-major)
-    double* gv = cuz + S::V_UZ;          // [EPB][3][4][NQ]
-    double* hv = gv + S::V_G;            // [EPB][4][4][NQF]
-    double* geo = hv + S::V_H;
-    double* ji = geo + S::GEO;
+    Real* tab = reinterpret_cast<Real*>(smem);
+    Real* cuz = tab + S::TAB;          // [EPB][20][NB]: U (5 rows), then Z (15 rows, d-major)
+    Real* gv = cuz + S::V_UZ;          // [EPB][3][4][NQ]
+    Real* hv = gv + S::V_G;            // [EPB][4][4][NQF]
+    Real* geo = hv + S::V_H;
+    Real* ji = geo + S::GEO;
     int* snbr = reinterpret_cast<int*>(ji + S::JI);
     const int tid = threadIdx.x;
-    const double mu = a.mu, kappa = a.kappa, gamma = a.gamma;
+    const Real mu = a.mu, kappa = a.kappa, gamma = a.gamma;
     for (int i = tid; i < S::TAB; i += NS_T) tab[i] = a.tab[i];
 
     const int64_t ntiles = (a.ne + EPB - 1) / EPB;
@@ -294,36 +299,36 @@ __global__ void __launch_bounds__(NS_T) k_ns_visc(NSArgs a) {
         for (int i = tid; i < nel * 4 * NQF; i += NS_T) {
             const int ef = i / NQF, q = i - ef * NQF;
             const int el = ef >> 2, f = ef & 3;
-            double W[20];
-            point_fields<NB, 20>(cuz + el * 20 * NB, tab + S::PHIF + f * NB * NQF + q, NQF, W);
-            const double* Zp = W + 5;
-            double Z[3][5];
+            Real W[20];
+            point_fields<Real, NB, 20>(cuz + el * 20 * NB, tab + S::PHIF + f * NB * NQF + q, NQF, W);
+            const Real* Zp = W + 5;
+            Real Z[3][5];
 #pragma unroll
             for (int d = 0; d < 3; ++d)
 #pragma unroll
                 for (int v = 0; v < 5; ++v) Z[d][v] = Zp[d * 5 + v];
             const int n = snbr[ef];
             const bool wall = n == -1 - DG_BC_WALL;
-            double Q[5];
+            Real Q[5];
             if (wall) wall_state(W, Q);
             else {
 #pragma unroll
                 for (int v = 0; v < 5; ++v) Q[v] = W[v];
             }
-            double F[3][5];
+            Real F[3][5];
             viscous_flux(Q, Z, mu, kappa, gamma, F);
-            const double* nr = geo + 4 * ef;
-            double Fn[4];
+            const Real* nr = geo + 4 * ef;
+            Real Fn[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v) Fn[v] = F[0][1 + v] * nr[0] + F[1][1 + v] * nr[1] + F[2][1 + v] * nr[2];
-            double w = nr[3];
+            Real w = nr[3];
             if (n >= 0) {
-                double* hb = a.HB + (((e0 + el) * 4 + f) * NQF + q) * 4;
+                Real* hb = a.HB + (((e0 + el) * 4 + f) * NQF + q) * 4;
 #pragma unroll
                 for (int v = 0; v < 4; ++v) hb[v] = Fn[v];
-                w *= 0.5;
+                w *= Real(0.5);
             } else if (wall) {
-                Fn[3] = 0.0;
+                Fn[3] = Real(0);
             }
 #pragma unroll
             for (int v = 0; v < 4; ++v) hv[(ef * 4 + v) * NQF + q] = w * Fn[v];
@@ -331,16 +336,16 @@ __global__ void __launch_bounds__(NS_T) k_ns_visc(NSArgs a) {
         // volume: contravariant viscous flux at every (element, point)
         for (int i = tid; i < nel * NQ; i += NS_T) {
             const int el = i / NQ, q = i - el * NQ;
-            double W[20];
-            point_fields<NB, 20>(cuz + el * 20 * NB, tab + S::PHIQ + q, NQ, W);
-            double Z[3][5];
+            Real W[20];
+            point_fields<Real, NB, 20>(cuz + el * 20 * NB, tab + S::PHIQ + q, NQ, W);
+            Real Z[3][5];
 #pragma unroll
             for (int d = 0; d < 3; ++d)
 #pragma unroll
                 for (int v = 0; v < 5; ++v) Z[d][v] = W[5 + d * 5 + v];
-            double F[3][5];
+            Real F[3][5];
             viscous_flux(W, Z, mu, kappa, gamma, F);
-            const double* I = ji + el * 9;
+            const Real* I = ji + el * 9;
 #pragma unroll
             for (int k = 0; k < 3; ++k)
 #pragma unroll
@@ -353,16 +358,16 @@ __global__ void __launch_bounds__(NS_T) k_ns_visc(NSArgs a) {
         for (int i = tid; i < nel * 4 * NB; i += NS_T) {
             const int ev = i / NB, j = i - ev * NB;
             const int el = ev >> 2, v = ev & 3;
-            double r = 0.0;
+            Real r = Real(0);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const double* g = gv + ((el * 3 + k) * 4 + v) * NQ;
+                const Real* g = gv + ((el * 3 + k) * 4 + v) * NQ;
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) r -= g[q] * tab[S::DPHIW + (k * NQ + q) * NB + j];
             }
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-                const double* h = hv + ((el * 4 + f) * 4 + v) * NQF;
+                const Real* h = hv + ((el * 4 + f) * 4 + v) * NQF;
 #pragma unroll
                 for (int q = 0; q < NQF; ++q) r += h[q] * tab[S::PHIFW + (f * NQF + q) * NB + j];
             }
@@ -371,14 +376,14 @@ __global__ void __launch_bounds__(NS_T) k_ns_visc(NSArgs a) {
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(NS_T) k_ns_lift(NSArgs a) {
+template <typename Real, int P>
+__global__ void __launch_bounds__(NS_T) k_ns_lift(NSArgs<Real> a) {
     using S = NSPlan<P>;
     constexpr int NB = S::NB, NQF = S::NQF, EPB = S::EPB;
     extern __shared__ __align__(16) unsigned char smem[];
-    double* lift = reinterpret_cast<double*>(smem);   // [4][NQF][NB] wf_q phi_j
-    double* hn = lift + 4 * NQF * NB;                  // [EPB][4][4][NQF]
-    double* sc = hn + EPB * 4 * 4 * NQF;              // [EPB][4] s_f / 2 (0 on boundary faces)
+    Real* lift = reinterpret_cast<Real*>(smem);   // [4][NQF][NB] wf_q phi_j
+    Real* hn = lift + 4 * NQF * NB;                  // [EPB][4][4][NQF]
+    Real* sc = hn + EPB * 4 * 4 * NQF;              // [EPB][4] s_f / 2 (0 on boundary faces)
     const int tid = threadIdx.x;
     for (int i = tid; i < 4 * NQF * NB; i += NS_T) lift[i] = a.tab[S::PHIFW + i];
 
@@ -388,23 +393,23 @@ __global__ void __launch_bounds__(NS_T) k_ns_lift(NSArgs a) {
         const int nel = (a.ne - e0) < (int64_t)EPB ? (int)(a.ne - e0) : EPB;
         __syncthreads();
         for (int i = tid; i < nel * 4; i += NS_T) {
-            const double* I = a.jinv + (e0 + (i >> 2)) * 9;
+            const Real* I = a.jinv + (e0 + (i >> 2)) * 9;
             const int f = i & 3;
-            double g[3];
+            Real g[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) g[d] = f == 0 ? -(I[d] + I[3 + d] + I[6 + d]) : I[3 * (f - 1) + d];
-            sc[i] = a.nbr[e0 * 4 + i] >= 0 ? 0.5 * sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) : 0.0;
+            sc[i] = a.nbr[e0 * 4 + i] >= 0 ? Real(0.5) * sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) : Real(0);
         }
         // the neighbour's entry at the matching point (the opposite normal flips its sign)
         for (int i = tid; i < nel * 4 * NQF; i += NS_T) {
             const int ef = i / NQF, q = i - ef * NQF;
             const int n = a.nbr[e0 * 4 + ef];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) hn[(ef * 4 + v) * NQF + q] = 0.0;
+            for (int v = 0; v < 4; ++v) hn[(ef * 4 + v) * NQF + q] = Real(0);
             if (n < 0) continue;
             const int code = a.fcode[e0 * 4 + ef];
             const int fn = code & 3, qn = a.fperm[(code >> 2) * NQF + q];
-            const double* hb = a.HB + (((int64_t)n * 4 + fn) * NQF + qn) * 4;
+            const Real* hb = a.HB + (((int64_t)n * 4 + fn) * NQF + qn) * 4;
 #pragma unroll
             for (int v = 0; v < 4; ++v) hn[(ef * 4 + v) * NQF + q] = -hb[v];
         }
@@ -412,11 +417,11 @@ __global__ void __launch_bounds__(NS_T) k_ns_lift(NSArgs a) {
         for (int i = tid; i < nel * 4 * NB; i += NS_T) {
             const int ev = i / NB, j = i - ev * NB;
             const int el = ev >> 2, v = ev & 3;
-            double r = 0.0;
+            Real r = Real(0);
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-                const double* h = hn + ((el * 4 + f) * 4 + v) * NQF;
-                double s = 0.0;
+                const Real* h = hn + ((el * 4 + f) * 4 + v) * NQF;
+                Real s = Real(0);
 #pragma unroll
                 for (int q = 0; q < NQF; ++q) s += h[q] * lift[(f * NQF + q) * NB + j];
                 r += sc[el * 4 + f] * s;
@@ -426,9 +431,8 @@ __global__ void __launch_bounds__(NS_T) k_ns_lift(NSArgs a) {
     }
 }
 
-template <typename K>
-cudaError_t launch_tiles(K kern, size_t bytes, int64_t ntiles, const NSArgs& args, cudaStream_t s, int nsm,
-                         int& occ) {
+template <typename K, typename A>
+cudaError_t launch_tiles(K kern, size_t bytes, int64_t ntiles, const A& args, cudaStream_t s, int nsm, int& occ) {
     if (occ < 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
@@ -441,66 +445,103 @@ cudaError_t launch_tiles(K kern, size_t bytes, int64_t ntiles, const NSArgs& arg
     return cudaGetLastError();
 }
 
-template <int P>
-cudaError_t ns_launch(const NSArgs& args, cudaStream_t s, int nsm) {
+template <typename Real, int P>
+cudaError_t ns_launch(const NSArgs<Real>& args, cudaStream_t s, int nsm) {
     using S = NSPlan<P>;
     static int occ_g = -1, occ_v = -1, occ_l = -1;
     const int64_t ntiles = (args.ne + S::EPB - 1) / S::EPB;
-    cudaError_t e = launch_tiles(k_ns_grad<P>, S::G_BYTES, ntiles, args, s, nsm, occ_g);
+    cudaError_t e = launch_tiles(k_ns_grad<Real, P>, S::g_bytes(sizeof(Real)), ntiles, args, s, nsm, occ_g);
     if (e != cudaSuccess) return e;
-    e = launch_tiles(k_ns_visc<P>, S::V_BYTES, ntiles, args, s, nsm, occ_v);
+    e = launch_tiles(k_ns_visc<Real, P>, S::v_bytes(sizeof(Real)), ntiles, args, s, nsm, occ_v);
     if (e != cudaSuccess) return e;
-    return launch_tiles(k_ns_lift<P>, S::L_BYTES, ntiles, args, s, nsm, occ_l);
+    return launch_tiles(k_ns_lift<Real, P>, S::l_bytes(sizeof(Real)), ntiles, args, s, nsm, occ_l);
 }
 
 }  // namespace
 
-size_t ns_face_buffer_doubles(int p, int64_t ne) { return (size_t)ne * 4 * nqf_of(p) * 4; }
+size_t ns_face_buffer_values(int p, int64_t ne) { return (size_t)ne * 4 * nqf_of(p) * 4; }
 
 namespace {
 // SSP-RK3 stage update from a stored residual: out = a U0 + b (U + dt R) (a = 0: U0 unread)
-__global__ void __launch_bounds__(256) k_rk_axpy(const double* __restrict__ U, const double* __restrict__ U0,
-                                                 const double* __restrict__ R, double* out, int64_t n, double dt,
-                                                 double a, double b) {
+template <typename Real>
+__global__ void __launch_bounds__(256) k_rk_axpy(const Real* __restrict__ U, const Real* __restrict__ U0,
+                                                 const Real* __restrict__ R, Real* out, int64_t n, Real dt, Real a,
+                                                 Real b) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double r = b * (U[i] + dt * R[i]);
-        if (a != 0.0) r += a * U0[i];
+        Real r = b * (U[i] + dt * R[i]);
+        if (a != Real(0)) r += a * U0[i];
         out[i] = r;
     }
 }
-}  // namespace
 
-cudaError_t launch_rk_axpy(const double* U, const double* U0, const double* R, double* out, int64_t n, double dt,
-                           double a, double b, cudaStream_t s) {
-    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
-    k_rk_axpy<<<(unsigned)blocks, 256, 0, s>>>(U, U0, R, out, n, dt, a, b);
-    return cudaGetLastError();
+// the same update of a float-float state (hi plane, then lo plane) from an FP32 residual, as the
+// mixed stage kernel's epilogue forms it: the increment a (U0 - U) + b dt R in FP32, added to
+// (hi, lo) with an error-free sum
+__global__ void __launch_bounds__(256) k_rk_axpy_ff(const float* __restrict__ U, const float* __restrict__ U0,
+                                                    const float* __restrict__ R, float* out, int64_t n, float bdt,
+                                                    float a) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float uh = U[i], ul = U[n + i];
+        const float dlt = a != 0.f ? fmaf(a, (U0[i] - uh) + (U0[n + i] - ul), bdt * R[i]) : bdt * R[i];
+        const float sm = uh + dlt;
+        const float bb = sm - uh;
+        const float err = ((uh - (sm - bb)) + (dlt - bb)) + ul;
+        const float oh = sm + err;
+        out[i] = oh;
+        out[n + i] = err - (oh - sm);
+    }
 }
 
-cudaError_t launch_ns_viscous(dg_mesh* m, const double* U, double* Z, double* HB, double* R, double mu,
-                              double prandtl, cudaStream_t s) {
-    NSArgs a;
-    a.U = U;
-    a.Z = Z;
-    a.R = R;
-    a.HB = HB;
+template <typename Real>
+cudaError_t ns_dispatch(dg_mesh* m, const void* U, void* Z, void* HB, void* R, double mu, double prandtl,
+                        cudaStream_t s) {
+    NSArgs<Real> a;
+    a.U = static_cast<const Real*>(U);
+    a.Z = static_cast<Real*>(Z);
+    a.R = static_cast<Real*>(R);
+    a.HB = static_cast<Real*>(HB);
     a.nbr = m->d_nbr;
     a.fcode = m->d_fcode;
-    a.jinv = m->d_jinv64;
-    a.tab = m->d_tab64;
+    a.jinv = static_cast<const Real*>(m->d_jinv);
+    a.tab = static_cast<const Real*>(m->d_tab);
     a.fperm = m->d_fperm;
     a.ne = m->host.ne;
-    a.mu = mu;
-    a.gamma = m->gamma;
-    a.kappa = mu * m->gamma / ((m->gamma - 1.0) * prandtl);
+    a.mu = (Real)mu;
+    a.gamma = (Real)m->gamma;
+    a.kappa = (Real)(mu * m->gamma / ((m->gamma - 1.0) * prandtl));
     int nsm = 0;
     cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
     if (e != cudaSuccess) return e;
     switch (m->p) {
-        case 1: return ns_launch<1>(a, s, nsm);
-        case 2: return ns_launch<2>(a, s, nsm);
-        default: return ns_launch<3>(a, s, nsm);
+        case 1: return ns_launch<Real, 1>(a, s, nsm);
+        case 2: return ns_launch<Real, 2>(a, s, nsm);
+        default: return ns_launch<Real, 3>(a, s, nsm);
     }
+}
+}  // namespace
+
+cudaError_t launch_rk_axpy(dg_mesh* m, const void* U, const void* U0, const void* R, void* out, double dt, double a,
+                           double b, cudaStream_t s) {
+    const int64_t n = m->host.ne * 5 * m->nb;
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    if (m->precision == DG_FP64)
+        k_rk_axpy<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(U), static_cast<const double*>(U0),
+                                                 static_cast<const double*>(R), static_cast<double*>(out), n, dt, a, b);
+    else if (m->precision == DG_FP32)
+        k_rk_axpy<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(U), static_cast<const float*>(U0),
+                                                static_cast<const float*>(R), static_cast<float*>(out), n, (float)dt,
+                                                (float)a, (float)b);
+    else
+        k_rk_axpy_ff<<<blocks, 256, 0, s>>>(static_cast<const float*>(U), static_cast<const float*>(U0),
+                                            static_cast<const float*>(R), static_cast<float*>(out), n,
+                                            (float)(b * dt), (float)a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ns_viscous(dg_mesh* m, const void* U, void* Z, void* HB, void* R, double mu, double prandtl,
+                              cudaStream_t s) {
+    if (m->precision == DG_FP64) return ns_dispatch<double>(m, U, Z, HB, R, mu, prandtl, s);
+    return ns_dispatch<float>(m, U, Z, HB, R, mu, prandtl, s);
 }
 
 }  // namespace dg
