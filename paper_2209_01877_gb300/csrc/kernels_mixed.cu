@@ -37,8 +37,7 @@
 // prepared inside this tile's phases, so no phase waits on their loads):
 //   MMA 1    own values at the 4 Nqf face points and the Nq volume points, from
 //            operand rows built during the previous tile's MMA 2; meanwhile the
-//            neighbours' traces (FP32), the per-element scaled J^-1 and
-//            mean-state fluxes, and the next tile's neighbour ids and L2
+//            neighbours' traces (FP32) and the next tile's neighbour ids and L2
 //            prefetch;
 //   stage    TMEM -> shared memory (FP32 point states; 16-lane TMEM loads so
 //            all 32 lanes of a warp work on the M = 64 accumulator); the next
@@ -48,8 +47,11 @@
 //            the owner's and, for in-tile faces, the partner's operand;
 //   MMA 2    projection onto the weighted basis gradients and face lift;
 //            meanwhile the epilogue's operands are loaded and the next tile's
-//            operand rows, slot codes and lists are built;
-//   epilogue R, or the RK stage in float-float, straight to global memory.
+//            operand rows, slot codes, lists and per-element records (scaled
+//            J^-1, mean-state fluxes; double-buffered) are built;
+//   epilogue R, or the RK stage in float-float, straight to global memory; no
+//            barrier closes the tile (the next tile's inputs were complete at
+//            the wait for MMA 2), so each warp goes on to the next tile.
 // Every wait on the tensor cores is bounded; on time-out the context sets a
 // status bit and leaves its tile loop (all its threads together); the CTA
 // frees its tensor memory when both contexts are done.
@@ -140,8 +142,8 @@ struct SPlan {
     static constexpr int X_ROW = a128(X_SN + SLOTS * 5 * NQF4 * 4);       // float2 [64] (mean, factor)
     // per slot, 3 float4: (n, sc), (sc Fbar.n)[0..3], ((sc Fbar.n)[4], staging offset, first K word, -)
     static constexpr int X_REC = a128(X_ROW + 64 * 8);
-    static constexpr int X_EL = a128(X_REC + SLOTS * 48);                 // float [ET][ELW]
-    static constexpr int X_CODE = a128(X_EL + ET * ELW * 4);              // uint32 [SLOTS]
+    static constexpr int X_EL = a128(X_REC + SLOTS * 48);                 // float [2][ET][ELW]: this tile's, the next's
+    static constexpr int X_CODE = a128(X_EL + 2 * ET * ELW * 4);          // uint32 [SLOTS]
     static constexpr int X_LIST = X_CODE + SLOTS * 4;                      // uint8 [2*SLOTS]: cross, work
     // int [THDR] header of the staged tile; int [SLOTS + 1] neighbour ids and cross count of the
     // tile whose neighbour blocks are copied next
@@ -270,6 +272,38 @@ __device__ __forceinline__ void issue_staged_blocks(const StageArgs& a, const in
     tc::cp_async_commit();
 }
 
+// per element of a tile: J^-1, its flux-scaled copy, the mean state's scaled contravariant flux and
+// flux, the scale, the epilogue factor and the A2 row parts of its 5 rows
+template <int NB, int K2>
+__device__ __forceinline__ void elem_setup(const StageArgs& a, int64_t ge, int e, float gamma, float* el) {
+    float I[9], ub[5];
+    const float* Ig = a.jinv + ge * 9;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) I[t] = __ldg(Ig + t);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) ub[v] = 2.449489743f * __ldg(a.U_hi + (ge * 5 + v) * NB);
+    const float ts = elem_flux_scale(ub, I, gamma);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        el[t] = I[t];
+        el[9 + t] = ts * I[t];
+    }
+    float G[3][5], F[3][5];
+    contravariant(ub, el + 9, gamma, G);
+    euler_fluxes(ub, gamma, F);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            el[18 + 5 * k + v] = G[k][v];
+            el[33 + 5 * k + v] = F[k][v];
+        }
+    el[48] = ts;
+    el[49] = a.inv_beta2 * __fdividef(1.f, ts);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) el[50 + v] = __int_as_float(rowpart(e * 5 + v, K2));
+}
+
 template <int P, int FLUX, bool BF, bool CONS>
 __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     using S = SPlan<P>;
@@ -292,7 +326,8 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     float* sN = reinterpret_cast<float*>(cx + S::X_SN);
     float2* sRow = reinterpret_cast<float2*>(cx + S::X_ROW);
     float4* sRec = reinterpret_cast<float4*>(cx + S::X_REC);
-    float* sEl = reinterpret_cast<float*>(cx + S::X_EL);
+    float* sEl = reinterpret_cast<float*>(cx + S::X_EL);   // this tile's element records
+    float* sEl2 = sEl + ET * ELW;                          // the next tile's
     uint32_t* sCode = reinterpret_cast<uint32_t*>(cx + S::X_CODE);
     uint8_t* sList = reinterpret_cast<uint8_t*>(cx + S::X_LIST);
     int* sHdr = reinterpret_cast<int*>(cx + S::X_HDR);
@@ -346,6 +381,11 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
     // the traces, the operand rows and metadata while MMA 2 runs
     if (tfirst < ntiles) {
         stage_tile_inputs<NB, K1, BF>(a, tfirst, ct, sA1, sRow, sCode, sList, sHdr);
+        if (ct >= 64 && ct < 64 + ET) {
+            const int64_t f0 = tfirst * ET;
+            const int e = ct - 64;
+            if (f0 + e < a.ne) elem_setup<NB, K2>(a, f0 + e, e, gamma, sEl + e * ELW);
+        }
         if (ct >= 128) {
             issue_neighbour_blocks<NV5>(a, tfirst, ct, sC);
             tc::cp_async_wait_all();
@@ -399,6 +439,12 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 prefetch_l2(a.jinv + n0 * 9, (uint32_t)(nn * 36));
                 prefetch_l2(a.slot + nt * SLOTS, SLOTS * 4);
                 prefetch_l2(a.tlist + nt * (2 * SLOTS), 2 * SLOTS);
+                // the neighbour ids and header of the tile after next (loaded during the next tile's MMA 1)
+                const int64_t n2 = nt + tstride;
+                if (n2 < ntiles) {
+                    prefetch_l2(a.xnbr + n2 * SLOTS, SLOTS * 4);
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.thdr + n2 * THDR));
+                }
             }
         }
         // the neighbours' traces at their face points (FP32, own point order of the neighbour's
@@ -436,41 +482,6 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
             float* nd = sN + c * 5 * NQF4 + p;
 #pragma unroll
             for (int v = 0; v < 5; ++v) nd[v * NQF4] = acc[v].x + acc[v].y;
-        }
-        // per element while the tensor cores work (used by the faces below and the flux phase)
-        if (ct >= 64 && ct < 64 + ET) {
-            // per element: J^-1, its flux-scaled copy, the mean state's flux and scaled
-            // contravariant flux, the scale and the epilogue factor
-            const int e = ct - 64;
-            if (e < nel) {
-                float I[9], ub[5];
-                const float* Ig = a.jinv + (e0 + e) * 9;
-#pragma unroll
-                for (int t = 0; t < 9; ++t) I[t] = __ldg(Ig + t);
-#pragma unroll
-                for (int v = 0; v < 5; ++v) ub[v] = 2.449489743f * __ldg(a.U_hi + ((e0 + e) * 5 + v) * NB);
-                const float ts = elem_flux_scale(ub, I, gamma);
-                float* el = sEl + e * ELW;
-#pragma unroll
-                for (int t = 0; t < 9; ++t) {
-                    el[t] = I[t];
-                    el[9 + t] = ts * I[t];
-                }
-                float G[3][5], F[3][5];
-                contravariant(ub, el + 9, gamma, G);
-                euler_fluxes(ub, gamma, F);
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-#pragma unroll
-                    for (int v = 0; v < 5; ++v) {
-                        el[18 + 5 * k + v] = G[k][v];
-                        el[33 + 5 * k + v] = F[k][v];
-                    }
-                el[48] = ts;
-                el[49] = a.inv_beta2 * __fdividef(1.f, ts);
-#pragma unroll
-                for (int v = 0; v < 5; ++v) el[50 + v] = __int_as_float(rowpart(e * 5 + v, K2));
-            }
         }
         if (ct >= 128 && ct < 160 && has_next) {
             const int i = ct - 128;
@@ -621,6 +632,15 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         // the next tile's operand rows and metadata (A1, the rows, codes and lists are free: MMA 1
         // and the flux phase are done)
         if (has_next) stage_tile_inputs<NB, K1, BF>(a, nt, ct, sA1, sRow, sCode, sList, sHdr);
+        // the next tile's element records (warp 7, otherwise idle here), into the other buffer: this
+        // tile's are still read by the epilogue
+        if (has_next && ct >= 224 && ct < 224 + ET) {
+            const int e = ct - 224;
+            if (nt * ET + e < a.ne) elem_setup<NB, K2>(a, nt * ET + e, e, gamma, sEl2 + e * ELW);
+        }
+        // the next tile's A1 rows are read by MMA 1, issued after the completion wait below: no
+        // barrier closes the tile
+        tc::fence_async_smem();
         // conservative mode: each (element, face, variable)'s flux integral from the split pairs
         // of the projection operand (read-only, like MMA 2): A2 = sc (H - Fbar.n), so
         // sum_q wf_q H_q = (sum_q wf_q A2_q + fb W) / sc with W = sum_q wf_q
@@ -688,6 +708,8 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 }
             }
         }
+        // this thread's epilogue factors
+        const float invA = okA ? sEl[(rA / 5) * ELW + 49] : 0.f, invB = okB ? sEl[(rB / 5) * ELW + 49] : 0.f;
         if (ct >= 128) tc::cp_async_wait_all();   // the next tile's neighbour blocks have landed
         if (!tc_wait(mbar, phase, ct, bar_id)) {
             if (ct == 0) atomicOr(a.status, 2u);
@@ -723,9 +745,8 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
             for (int rr = 0; rr < 2; ++rr) {
                 const bool ok = rr == 0 ? okA : okB;
                 if (!ok) continue;
-                const int r = rr == 0 ? rA : rB;
                 const int64_t g = rr == 0 ? gA : gB;
-                const float inv = sEl[(r / 5) * ELW + 49];
+                const float inv = rr == 0 ? invA : invB;
                 const float2 R = mul2(dp[rr], f2(inv));
                 // conservative mode: mode 0 is k_cons_mode0's, in FP64 (left unwritten here)
                 const bool skip0 = CONS && j0 == 0;
@@ -767,10 +788,9 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 }
             }
         }
-        tc::fence_async_smem();   // the next tile's A1 rows, written above, are read by MMA 1
-        tc::fence_before();
-        ctx_sync(bar_id);
-        tc::fence_after();
+        float* const done = sEl;   // the next tile's records become the current ones
+        sEl = sEl2;
+        sEl2 = done;
     }
     if (ct == 0) tc::commit(mbar + 1);
     tc::cp_async_wait_all();   // no copy outlives the context (a timed-out loop may leave one)
