@@ -37,18 +37,19 @@
 // prepared inside this tile's phases, so no phase waits on their loads):
 //   MMA 1    own values at the 4 Nqf face points and the Nq volume points, from
 //            operand rows built during the previous tile's MMA 2; meanwhile the
-//            neighbours' traces (FP32) and the next tile's neighbour ids and L2
-//            prefetch;
+//            neighbours' traces (FP32), the next tile's neighbour ids (loaded
+//            one tile earlier) and the L2 prefetch of its blocks;
 //   stage    TMEM -> shared memory (FP32 point states; 16-lane TMEM loads so
 //            all 32 lanes of a warp work on the M = 64 accumulator); the next
 //            tile's neighbour blocks are requested by cp.async;
 //   flux     volume points: contravariant flux deviation; face points:
 //            Rusanov / Roe flux (ghost state on boundary faces) written to
-//            the owner's and, for in-tile faces, the partner's operand;
+//            the owner's and, for in-tile faces, the partner's operand; then
+//            warp 7, the least loaded, builds the next tile's per-element
+//            records (scaled J^-1, mean-state fluxes; double-buffered);
 //   MMA 2    projection onto the weighted basis gradients and face lift;
 //            meanwhile the epilogue's operands are loaded and the next tile's
-//            operand rows, slot codes, lists and per-element records (scaled
-//            J^-1, mean-state fluxes; double-buffered) are built;
+//            operand rows, slot codes and lists are built;
 //   epilogue R, or the RK stage in float-float, straight to global memory; no
 //            barrier closes the tile (the next tile's inputs were complete at
 //            the wait for MMA 2), so each warp goes on to the next tile.
@@ -391,6 +392,16 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
             tc::cp_async_wait_all();
         }
     }
+    // the neighbour ids and cross count of this context's second tile, carried in registers (warp 4):
+    // each tile stores the ids of its next tile and loads those of the tile after
+    int xc0 = 0, xc1 = 0, xcc = 0;
+    if (ct >= 128 && ct < 160 && tfirst + tstride < ntiles) {
+        const int i = ct - 128;
+        const int64_t n1 = tfirst + tstride;
+        xc0 = __ldg(a.xnbr + n1 * SLOTS + i);
+        if (i + 32 < SLOTS) xc1 = __ldg(a.xnbr + n1 * SLOTS + i + 32);
+        if (i == 0) xcc = __ldg(a.thdr + n1 * THDR);
+    }
     tc::fence_async_smem();
     tc::fence_before();
     ctx_sync(bar_id);
@@ -416,15 +427,20 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                     tc::mma(tmem + S::C_D1, dA1 + KSTEP * ks, dT1[h] + KSTEP * ks, id1, (h | ks) != 0);
             tc::commit(mbar);
         }
-        // the next tile: neighbour ids and cross count into sXn (loads issued here, stored after
-        // this thread's traces), and an L2 prefetch of its contiguous blocks
-        int xn0 = 0, xn1 = 0, xnc = 0;
+        // the next tile's neighbour ids into sXn (loaded during the previous tile), the loads of the
+        // tile after next, and an L2 prefetch of the next tile's contiguous blocks
         if (ct >= 128 && ct < 160 && has_next) {
             const int i = ct - 128;
-            xn0 = __ldg(a.xnbr + nt * SLOTS + i);
-            if (i + 32 < SLOTS) xn1 = __ldg(a.xnbr + nt * SLOTS + i + 32);
+            sXn[i] = xc0;
+            if (i + 32 < SLOTS) sXn[i + 32] = xc1;
+            if (i == 0) sXn[SLOTS] = xcc;
+            const int64_t n2 = nt + tstride;
+            if (n2 < ntiles) {
+                xc0 = __ldg(a.xnbr + n2 * SLOTS + i);
+                if (i + 32 < SLOTS) xc1 = __ldg(a.xnbr + n2 * SLOTS + i + 32);
+                if (i == 0) xcc = __ldg(a.thdr + n2 * THDR);
+            }
             if (i == 0) {
-                xnc = __ldg(a.thdr + nt * THDR);
                 const int64_t n0 = nt * ET;
                 const int nn = (a.ne - n0) < (int64_t)ET ? (int)(a.ne - n0) : ET;
                 const uint32_t sb = (uint32_t)(nn * 5 * NB * 4);
@@ -439,12 +455,6 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 prefetch_l2(a.jinv + n0 * 9, (uint32_t)(nn * 36));
                 prefetch_l2(a.slot + nt * SLOTS, SLOTS * 4);
                 prefetch_l2(a.tlist + nt * (2 * SLOTS), 2 * SLOTS);
-                // the neighbour ids and header of the tile after next (loaded during the next tile's MMA 1)
-                const int64_t n2 = nt + tstride;
-                if (n2 < ntiles) {
-                    prefetch_l2(a.xnbr + n2 * SLOTS, SLOTS * 4);
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.thdr + n2 * THDR));
-                }
             }
         }
         // the neighbours' traces at their face points (FP32, own point order of the neighbour's
@@ -482,12 +492,6 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
             float* nd = sN + c * 5 * NQF4 + p;
 #pragma unroll
             for (int v = 0; v < 5; ++v) nd[v * NQF4] = acc[v].x + acc[v].y;
-        }
-        if (ct >= 128 && ct < 160 && has_next) {
-            const int i = ct - 128;
-            sXn[i] = xn0;
-            if (i + 32 < SLOTS) sXn[i + 32] = xn1;
-            if (i == 0) sXn[SLOTS] = xnc;
         }
         if (!tc_wait(mbar, phase, ct, bar_id)) {
             if (ct == 0) atomicOr(a.status, 2u);
@@ -611,6 +615,13 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
                 }
             }
         }
+        // the next tile's element records into the other buffer (this tile's are still read by the
+        // epilogue), by warp 7: the flux items come to it last in every round, so it is the least
+        // loaded warp of the flux phase
+        if (has_next && ct >= 224 && ct < 224 + ET) {
+            const int e = ct - 224;
+            if (nt * ET + e < a.ne) elem_setup<NB, K2>(a, nt * ET + e, e, gamma, sEl2 + e * ELW);
+        }
         tc::fence_async_smem();
         tc::fence_before();
         ctx_sync(bar_id);
@@ -632,12 +643,6 @@ __global__ void __launch_bounds__(MT, 1) k_stage_mixed(StageArgs a) {
         // the next tile's operand rows and metadata (A1, the rows, codes and lists are free: MMA 1
         // and the flux phase are done)
         if (has_next) stage_tile_inputs<NB, K1, BF>(a, nt, ct, sA1, sRow, sCode, sList, sHdr);
-        // the next tile's element records (warp 7, otherwise idle here), into the other buffer: this
-        // tile's are still read by the epilogue
-        if (has_next && ct >= 224 && ct < 224 + ET) {
-            const int e = ct - 224;
-            if (nt * ET + e < a.ne) elem_setup<NB, K2>(a, nt * ET + e, e, gamma, sEl2 + e * ELW);
-        }
         // the next tile's A1 rows are read by MMA 1, issued after the completion wait below: no
         // barrier closes the tile
         tc::fence_async_smem();
