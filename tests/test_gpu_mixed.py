@@ -31,7 +31,7 @@ TOLMIX = 5e-6
 TOLBF = 3e-4
 
 
-# element orders: a space-filling curve puts most faces inside one 24-element tile (evaluated
+# element orders: a space-filling curve puts most faces inside one 12-element tile (evaluated
 # once, flux written to both sides); reverse Cuthill-McKee puts none there (every face takes the
 # neighbour-trace path)
 ORDERS = {"morton": dg.DG_ORDER_MORTON, "rcm": dg.DG_ORDER_RCM}
@@ -120,10 +120,10 @@ def test_mixed_bf16_box_and_rk_steps():
 
 
 def test_mixed_ragged_tile_and_free_stream():
-    """A mesh whose element count is not a multiple of the 24-element tile,
+    """A mesh whose element count is not a multiple of the 12-element tile,
     and free-stream preservation through the tensor-core path."""
-    m = I.make_box_mesh((3, 2, 3), periodic=(True, True, True), jitter=0.15)
-    assert m.ne % 24 != 0
+    m = I.make_box_mesh((3, 3, 3), periodic=(True, True, True), jitter=0.15)
+    assert m.ne % 12 != 0
     P = Problem(m.tet_vid, m.tet_xyz, None, p=3, flux="roe")
     U = vortex_state(P, radius=0.2)
     for order in ORDERS:
@@ -132,6 +132,30 @@ def test_mixed_ragged_tile_and_free_stream():
     Uf = P.project(I.uniform_flow)
     Rf = gpu_residual(_mesh(m, 3, "roe"), Uf)
     assert np.abs(Rf).max() < 1e-5 * max(residual_term_scale(P, Uf))
+
+
+def test_mixed_many_tiles_per_pipeline():
+    """20,250 elements: 1,688 tiles of 12, the last one partial, so each of the 304 tile
+    pipelines of a 152-SM grid runs 5-6 tiles and its steady state -- the next tile's
+    neighbour ids loaded a tile ahead, element records double-buffered, no barrier between
+    tiles -- in the residual (Morton and RCM order) and in the three RK stages."""
+    m = I.make_periodic_cube(15, jitter=0.15)
+    assert m.ne % 12 != 0 and (m.ne + 11) // 12 > 4 * 2 * 152
+    P = Problem(m.tet_vid, m.tet_xyz, None, p=3, flux="roe")
+    U0 = vortex_state(P, radius=0.15)
+    R = P.residual(U0)
+    ts = residual_term_scale(P, U0)
+    for order in ORDERS:
+        assert max_rel_err(gpu_residual(_mesh(m, 3, "roe", order=order), U0), R, term_scale=ts) < TOLMIX
+    dt = P.stable_dt(U0, 0.1)
+    ref = P.rk3(U0, dt, 2)
+    M = _mesh(m, 3, "roe")
+    dg.dg_set_state(M.handle, U0)
+    dg.dg_rk3_step(M.handle, dt, 2)
+    U = np.empty_like(U0)
+    dg.dg_get_state(M.handle, U)
+    dg.dg_sync_status(M.handle)
+    assert np.abs(U - ref).max() < 1e-6 * np.abs(ref).max()
 
 
 def test_mixed_rk_steps_track_fp64():
