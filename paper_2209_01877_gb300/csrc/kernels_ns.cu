@@ -53,10 +53,16 @@ struct NSPlan {
     static constexpr int PHIQ = 0, DPHIW = NB * NQ, PHIF = DPHIW + 3 * NQ * NB, PHIFW = PHIF + 4 * NB * NQF,
                          TAB = PHIFW + 4 * NQF * NB;
     static constexpr int GEO = EPB * 4 * 4, JI = EPB * 9;
-    // gradient pass: own blocks, neighbour blocks (then the volume values), s Qhat
-    static constexpr int G_OWN = EPB * 5 * NB, G_NBR = EPB * 4 * 5 * NB, G_QH = EPB * 4 * 5 * NQF;
-    static_assert(EPB * 5 * NQ <= G_NBR, "volume values fit the neighbour blocks");
-    static constexpr int G_REALS = TAB + G_OWN + G_NBR + G_QH + GEO + JI;
+    // gradient pass, for an element size rs: the own blocks [EPB][NB][NFP] and the neighbour blocks
+    // [EPB][4][NB][NFP] mode-major, NFP = nfp(rs) reals per mode (the 5 variables in a 16-byte-
+    // aligned row: 8 floats or 6 doubles); the volume values [EPB][NQ][NFP] then reuse the
+    // neighbour blocks' space; s Qhat [EPB][4][NQF][NFP]
+    static constexpr int nfp(size_t rs) { return rs == 4 ? 8 : 6; }
+    static constexpr int g_own(size_t rs) { return EPB * NB * nfp(rs); }
+    static constexpr int g_nbr(size_t rs) { return EPB * 4 * NB * nfp(rs); }
+    static constexpr int g_qh(size_t rs) { return EPB * 4 * NQF * nfp(rs); }
+    static_assert(NQ <= 4 * NB, "volume values fit the neighbour blocks");
+    static constexpr int g_reals(size_t rs) { return TAB + g_own(rs) + g_nbr(rs) + g_qh(rs) + GEO + JI; }
     // viscous pass: U and Z blocks, contravariant viscous flux (momentum + energy), s H_own
     static constexpr int V_UZ = EPB * 20 * NB, V_G = EPB * 3 * 4 * NQ, V_H = EPB * 4 * 4 * NQF;
     static constexpr int V_REALS = TAB + V_UZ + V_G + V_H + GEO + JI;
@@ -64,7 +70,7 @@ struct NSPlan {
     static constexpr int L_REALS = 4 * NQF * NB + EPB * 4 * 4 * NQF + EPB * 4;
     static constexpr size_t ints = EPB * 4 * sizeof(int) + EPB * 4 + 6 * NQF + 16;
     // shared-memory bytes for an element size rs (8 FP64, 4 FP32)
-    static constexpr size_t g_bytes(size_t rs) { return G_REALS * rs + ints; }
+    static constexpr size_t g_bytes(size_t rs) { return g_reals(rs) * rs + ints; }
     static constexpr size_t v_bytes(size_t rs) { return V_REALS * rs + ints; }
     static constexpr size_t l_bytes(size_t rs) { return L_REALS * rs + ints; }
 };
@@ -156,16 +162,78 @@ __device__ __forceinline__ void point_fields(const Real* c, const Real* phi, int
     }
 }
 
+// four consecutive Reals of shared memory (16-byte aligned) in one or two vector accesses
+__device__ __forceinline__ void ld4(const float* p, float (&x)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+    x[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&x)[4]) {
+    const double2 v0 = *reinterpret_cast<const double2*>(p), v1 = *reinterpret_cast<const double2*>(p + 2);
+    x[0] = v0.x;
+    x[1] = v0.y;
+    x[2] = v1.x;
+    x[3] = v1.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&x)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&x)[4]) {
+    *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(x[2], x[3]);
+}
+
+// the same sums as point_fields over mode-major coefficients cm[j * NF + v] (rows 16-byte aligned,
+// NF a multiple of 4): each mode's NF values come in NF / 4 vector loads, and every field
+// accumulates over j in the same order
+template <typename Real, int NB, int NF>
+__device__ __forceinline__ void point_fields_mm(const Real* cm, const Real* phi, int stride, Real* out) {
+    static_assert(NF % 4 == 0, "whole vectors per mode");
+#pragma unroll
+    for (int v = 0; v < NF; ++v) out[v] = Real(0);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        const Real t = phi[j * stride];
+#pragma unroll
+        for (int v = 0; v < NF; v += 4) {
+            Real x[4];
+            ld4(cm + j * NF + v, x);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) out[v + u] += x[u] * t;
+        }
+    }
+}
+
+// the same sums as point_fields<Real, NB, 5> over mode-major coefficients cm[j * NFP + v]
+// (rows 16-byte aligned): per mode one vector load of variables 0-3 and one load of variable 4
+template <typename Real, int NB, int NFP>
+__device__ __forceinline__ void point_fields5_mm(const Real* cm, const Real* phi, int stride, Real* out) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[v] = Real(0);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        const Real t = phi[j * stride];
+        Real x[4];
+        ld4(cm + j * NFP, x);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) out[u] += x[u] * t;
+        out[4] += cm[j * NFP + 4] * t;
+    }
+}
+
 template <typename Real, int P>
 __global__ void __launch_bounds__(NS_T) k_ns_grad(NSArgs<Real> a) {
     using S = NSPlan<P>;
     constexpr int NB = S::NB, NQ = S::NQ, NQF = S::NQF, EPB = S::EPB;
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NFP = S::nfp(sizeof(Real));
     Real* tab = reinterpret_cast<Real*>(smem);
-    Real* cown = tab + S::TAB;
-    Real* big = cown + S::G_OWN;
-    Real* hq = big + S::G_NBR;
-    Real* geo = hq + S::G_QH;
+    Real* cown = tab + S::TAB;                    // [EPB][NB][NFP]
+    Real* big = cown + S::g_own(sizeof(Real));    // [EPB][4][NB][NFP], then the volume values [EPB][NQ][NFP]
+    Real* hq = big + S::g_nbr(sizeof(Real));      // [EPB][4][NQF][NFP]
+    Real* geo = hq + S::g_qh(sizeof(Real));
     Real* ji = geo + S::GEO;
     int* snbr = reinterpret_cast<int*>(ji + S::JI);
     uint8_t* sfc = reinterpret_cast<uint8_t*>(snbr + EPB * 4);
@@ -179,7 +247,10 @@ __global__ void __launch_bounds__(NS_T) k_ns_grad(NSArgs<Real> a) {
         const int64_t e0 = tile * EPB;
         const int nel = (a.ne - e0) < (int64_t)EPB ? (int)(a.ne - e0) : EPB;
         __syncthreads();
-        for (int i = tid; i < nel * 5 * NB; i += NS_T) cown[i] = a.U[e0 * 5 * NB + i];
+        for (int i = tid; i < nel * 5 * NB; i += NS_T) {
+            const int el = i / (5 * NB), k = i - el * 5 * NB, v = k / NB, j = k - v * NB;
+            cown[(el * NB + j) * NFP + v] = a.U[e0 * 5 * NB + i];
+        }
         for (int i = tid; i < nel * 4; i += NS_T) {
             snbr[i] = a.nbr[e0 * 4 + i];
             sfc[i] = a.fcode[e0 * 4 + i];
@@ -187,9 +258,9 @@ __global__ void __launch_bounds__(NS_T) k_ns_grad(NSArgs<Real> a) {
         for (int i = tid; i < nel * 9; i += NS_T) ji[i] = a.jinv[e0 * 9 + i];
         __syncthreads();
         for (int i = tid; i < nel * 4 * 5 * NB; i += NS_T) {
-            const int ef = i / (5 * NB), k = i - ef * 5 * NB;
+            const int ef = i / (5 * NB), k = i - ef * 5 * NB, v = k / NB, j = k - v * NB;
             const int n = snbr[ef];
-            big[i] = n >= 0 ? a.U[(int64_t)n * 5 * NB + k] : Real(0);
+            big[(ef * NB + j) * NFP + v] = n >= 0 ? a.U[(int64_t)n * 5 * NB + k] : Real(0);
         }
         tile_geometry(ji, nel, tid, geo);
         __syncthreads();
@@ -198,13 +269,13 @@ __global__ void __launch_bounds__(NS_T) k_ns_grad(NSArgs<Real> a) {
             const int ef = i / NQF, q = i - ef * NQF;
             const int el = ef >> 2, f = ef & 3;
             Real Um[5], Qh[5];
-            point_fields<Real, NB, 5>(cown + el * 5 * NB, tab + S::PHIF + f * NB * NQF + q, NQF, Um);
+            point_fields5_mm<Real, NB, NFP>(cown + el * NB * NFP, tab + S::PHIF + f * NB * NQF + q, NQF, Um);
             const int n = snbr[ef];
             if (n >= 0) {
                 const int code = sfc[ef];
                 const int fn = code & 3, qn = sperm[(code >> 2) * NQF + q];
                 Real Up[5];
-                point_fields<Real, NB, 5>(big + ef * 5 * NB, tab + S::PHIF + fn * NB * NQF + qn, NQF, Up);
+                point_fields5_mm<Real, NB, NFP>(big + ef * NB * NFP, tab + S::PHIF + fn * NB * NQF + qn, NQF, Up);
 #pragma unroll
                 for (int v = 0; v < 5; ++v) Qh[v] = Real(0.5) * (Um[v] + Up[v]);
             } else if (n == -1 - DG_BC_WALL) {
@@ -215,48 +286,68 @@ __global__ void __launch_bounds__(NS_T) k_ns_grad(NSArgs<Real> a) {
             }
             const Real s = geo[4 * ef + 3];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) hq[(ef * 5 + v) * NQF + q] = s * Qh[v];
+            for (int v = 0; v < 5; ++v) hq[(ef * NQF + q) * NFP + v] = s * Qh[v];
         }
         __syncthreads();
         // volume: Q at every (element, point), over the neighbour blocks
         for (int i = tid; i < nel * NQ; i += NS_T) {
             const int el = i / NQ, q = i - el * NQ;
             Real Uq[5];
-            point_fields<Real, NB, 5>(cown + el * 5 * NB, tab + S::PHIQ + q, NQ, Uq);
+            point_fields5_mm<Real, NB, NFP>(cown + el * NB * NFP, tab + S::PHIQ + q, NQ, Uq);
 #pragma unroll
-            for (int v = 0; v < 5; ++v) big[(el * 5 + v) * NQ + q] = Uq[v];
+            for (int v = 0; v < 5; ++v) big[(el * NQ + q) * NFP + v] = Uq[v];
         }
         __syncthreads();
-        // the three gradient components of mode j of variable v
-        for (int i = tid; i < nel * 5 * NB; i += NS_T) {
-            const int ev = i / NB, j = i - ev * NB;
-            const int el = ev / 5, v = ev - el * 5;
-            Real t[3];
-            const Real* uq = big + ev * NQ;
+        // the three gradient components of mode j of the 5 variables: thread per (element, mode),
+        // one table value and one vector load (plus variable 4) per term
+        for (int i = tid; i < nel * NB; i += NS_T) {
+            const int el = i / NB, j = i - el * NB;
+            Real t[5][3];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) t[v][0] = t[v][1] = t[v][2] = Real(0);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                Real s = Real(0);
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) s += uq[q] * tab[S::DPHIW + (k * NQ + q) * NB + j];
-                t[k] = s;
+                for (int q = 0; q < NQ; ++q) {
+                    const Real w = tab[S::DPHIW + (k * NQ + q) * NB + j];
+                    const Real* uq = big + (el * NQ + q) * NFP;
+                    Real x[4];
+                    ld4(uq, x);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) t[u][k] += x[u] * w;
+                    t[4][k] += uq[4] * w;
+                }
             }
             const Real* I = ji + el * 9;
-            Real z[3];
+            Real z[5][3];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) z[d] = -(I[d] * t[0] + I[3 + d] * t[1] + I[6 + d] * t[2]);
+            for (int v = 0; v < 5; ++v)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) z[v][d] = -(I[d] * t[v][0] + I[3 + d] * t[v][1] + I[6 + d] * t[v][2]);
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-                const Real* h = hq + ((el * 4 + f) * 5 + v) * NQF;
-                Real s = Real(0);
+                Real sf[5] = {Real(0), Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
-                for (int q = 0; q < NQF; ++q) s += h[q] * tab[S::PHIFW + (f * NQF + q) * NB + j];
+                for (int q = 0; q < NQF; ++q) {
+                    const Real w = tab[S::PHIFW + (f * NQF + q) * NB + j];
+                    const Real* h = hq + ((el * 4 + f) * NQF + q) * NFP;
+                    Real x[4];
+                    ld4(h, x);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) sf[u] += x[u] * w;
+                    sf[4] += h[4] * w;
+                }
                 const Real* nr = geo + 4 * (el * 4 + f);
 #pragma unroll
-                for (int d = 0; d < 3; ++d) z[d] += nr[d] * s;
+                for (int v = 0; v < 5; ++v)
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) z[v][d] += nr[d] * sf[v];
             }
             const int64_t e = e0 + el;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) a.Z[((e * 3 + d) * 5 + v) * NB + j] = z[d];
+            for (int v = 0; v < 5; ++v)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) a.Z[((e * 3 + d) * 5 + v) * NB + j] = z[v][d];
         }
     }
 }
@@ -267,9 +358,11 @@ __global__ void __launch_bounds__(NS_T) k_ns_visc(NSArgs<Real> a) {
     constexpr int NB = S::NB, NQ = S::NQ, NQF = S::NQF, EPB = S::EPB;
     extern __shared__ __align__(16) unsigned char smem[];
     Real* tab = reinterpret_cast<Real*>(smem);
-    Real* cuz = tab + S::TAB;          // [EPB][20][NB]: U (5 rows), then Z (15 rows, d-major)
-    Real* gv = cuz + S::V_UZ;          // [EPB][3][4][NQ]
-    Real* hv = gv + S::V_G;            // [EPB][4][4][NQF]
+    // U and Z mode-major: per element and mode, U (5 values), then Z (15, d-major); the momentum
+    // and energy rows of the contravariant viscous flux and of the face flux innermost
+    Real* cuz = tab + S::TAB;          // [EPB][NB][20]
+    Real* gv = cuz + S::V_UZ;          // [EPB][3][NQ][4]
+    Real* hv = gv + S::V_G;            // [EPB][4][NQF][4]
     Real* geo = hv + S::V_H;
     Real* ji = geo + S::GEO;
     int* snbr = reinterpret_cast<int*>(ji + S::JI);
@@ -283,12 +376,12 @@ __global__ void __launch_bounds__(NS_T) k_ns_visc(NSArgs<Real> a) {
         const int nel = (a.ne - e0) < (int64_t)EPB ? (int)(a.ne - e0) : EPB;
         __syncthreads();
         for (int i = tid; i < nel * 5 * NB; i += NS_T) {
-            const int el = i / (5 * NB), k = i - el * 5 * NB;
-            cuz[el * 20 * NB + k] = a.U[e0 * 5 * NB + i];
+            const int el = i / (5 * NB), k = i - el * 5 * NB, v = k / NB, j = k - v * NB;
+            cuz[(el * NB + j) * 20 + v] = a.U[e0 * 5 * NB + i];
         }
         for (int i = tid; i < nel * 15 * NB; i += NS_T) {
-            const int el = i / (15 * NB), k = i - el * 15 * NB;
-            cuz[el * 20 * NB + 5 * NB + k] = a.Z[e0 * 15 * NB + i];
+            const int el = i / (15 * NB), k = i - el * 15 * NB, r = k / NB, j = k - r * NB;
+            cuz[(el * NB + j) * 20 + 5 + r] = a.Z[e0 * 15 * NB + i];
         }
         for (int i = tid; i < nel * 4; i += NS_T) snbr[i] = a.nbr[e0 * 4 + i];
         for (int i = tid; i < nel * 9; i += NS_T) ji[i] = a.jinv[e0 * 9 + i];
@@ -300,7 +393,7 @@ __global__ void __launch_bounds__(NS_T) k_ns_visc(NSArgs<Real> a) {
             const int ef = i / NQF, q = i - ef * NQF;
             const int el = ef >> 2, f = ef & 3;
             Real W[20];
-            point_fields<Real, NB, 20>(cuz + el * 20 * NB, tab + S::PHIF + f * NB * NQF + q, NQF, W);
+            point_fields_mm<Real, NB, 20>(cuz + el * NB * 20, tab + S::PHIF + f * NB * NQF + q, NQF, W);
             const Real* Zp = W + 5;
             Real Z[3][5];
 #pragma unroll
@@ -330,14 +423,16 @@ __global__ void __launch_bounds__(NS_T) k_ns_visc(NSArgs<Real> a) {
             } else if (wall) {
                 Fn[3] = Real(0);
             }
+            Real h[4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) hv[(ef * 4 + v) * NQF + q] = w * Fn[v];
+            for (int v = 0; v < 4; ++v) h[v] = w * Fn[v];
+            st4(hv + (ef * NQF + q) * 4, h);
         }
         // volume: contravariant viscous flux at every (element, point)
         for (int i = tid; i < nel * NQ; i += NS_T) {
             const int el = i / NQ, q = i - el * NQ;
             Real W[20];
-            point_fields<Real, NB, 20>(cuz + el * 20 * NB, tab + S::PHIQ + q, NQ, W);
+            point_fields_mm<Real, NB, 20>(cuz + el * NB * 20, tab + S::PHIQ + q, NQ, W);
             Real Z[3][5];
 #pragma unroll
             for (int d = 0; d < 3; ++d)
@@ -347,31 +442,43 @@ __global__ void __launch_bounds__(NS_T) k_ns_visc(NSArgs<Real> a) {
             viscous_flux(W, Z, mu, kappa, gamma, F);
             const Real* I = ji + el * 9;
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
+            for (int k = 0; k < 3; ++k) {
+                Real g[4];
 #pragma unroll
-                for (int v = 0; v < 4; ++v)
-                    gv[((el * 3 + k) * 4 + v) * NQ + q] =
-                        I[3 * k] * F[0][1 + v] + I[3 * k + 1] * F[1][1 + v] + I[3 * k + 2] * F[2][1 + v];
+                for (int v = 0; v < 4; ++v) g[v] = I[3 * k] * F[0][1 + v] + I[3 * k + 1] * F[1][1 + v] + I[3 * k + 2] * F[2][1 + v];
+                st4(gv + ((el * 3 + k) * NQ + q) * 4, g);
+            }
         }
         __syncthreads();
-        // projection and own face lift of the momentum and energy rows, added to R
-        for (int i = tid; i < nel * 4 * NB; i += NS_T) {
-            const int ev = i / NB, j = i - ev * NB;
-            const int el = ev >> 2, v = ev & 3;
-            Real r = Real(0);
+        // projection and own face lift of the momentum and energy rows, added to R: thread per
+        // (element, mode), the four rows from one table value and one vector load per term
+        for (int i = tid; i < nel * NB; i += NS_T) {
+            const int el = i / NB, j = i - el * NB;
+            Real r[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const Real* g = gv + ((el * 3 + k) * 4 + v) * NQ;
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) r -= g[q] * tab[S::DPHIW + (k * NQ + q) * NB + j];
+                for (int q = 0; q < NQ; ++q) {
+                    const Real t = tab[S::DPHIW + (k * NQ + q) * NB + j];
+                    Real g[4];
+                    ld4(gv + ((el * 3 + k) * NQ + q) * 4, g);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) r[v] -= g[v] * t;
+                }
             }
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-                const Real* h = hv + ((el * 4 + f) * 4 + v) * NQF;
 #pragma unroll
-                for (int q = 0; q < NQF; ++q) r += h[q] * tab[S::PHIFW + (f * NQF + q) * NB + j];
+                for (int q = 0; q < NQF; ++q) {
+                    const Real t = tab[S::PHIFW + (f * NQF + q) * NB + j];
+                    Real h[4];
+                    ld4(hv + ((el * 4 + f) * NQF + q) * 4, h);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) r[v] += h[v] * t;
+                }
             }
-            a.R[((e0 + el) * 5 + 1 + v) * NB + j] += r;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) a.R[((e0 + el) * 5 + 1 + v) * NB + j] += r[v];
         }
     }
 }
