@@ -149,19 +149,6 @@ __device__ __forceinline__ void wall_state(const Real U[5], Real Q[5]) {
     Q[4] = U[4] - Real(0.5) * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0];
 }
 
-// values at one point of nf fields whose coefficient rows (NB each) start at c, basis values
-// phi[j * stride]
-template <typename Real, int NB, int NF>
-__device__ __forceinline__ void point_fields(const Real* c, const Real* phi, int stride, Real* out) {
-#pragma unroll
-    for (int v = 0; v < NF; ++v) {
-        Real s = Real(0);
-#pragma unroll
-        for (int j = 0; j < NB; ++j) s += c[v * NB + j] * phi[j * stride];
-        out[v] = s;
-    }
-}
-
 // four consecutive Reals of shared memory (16-byte aligned) in one or two vector accesses
 __device__ __forceinline__ void ld4(const float* p, float (&x)[4]) {
     const float4 v = *reinterpret_cast<const float4*>(p);
@@ -185,9 +172,9 @@ __device__ __forceinline__ void st4(double* p, const double (&x)[4]) {
     *reinterpret_cast<double2*>(p + 2) = make_double2(x[2], x[3]);
 }
 
-// the same sums as point_fields over mode-major coefficients cm[j * NF + v] (rows 16-byte aligned,
-// NF a multiple of 4): each mode's NF values come in NF / 4 vector loads, and every field
-// accumulates over j in the same order
+// values at one point of NF fields, out[v] = sum_j cm[j * NF + v] phi[j * stride] summed in
+// increasing j, from mode-major coefficients (rows 16-byte aligned, NF a multiple of 4): each
+// mode's NF values come in NF / 4 vector loads
 template <typename Real, int NB, int NF>
 __device__ __forceinline__ void point_fields_mm(const Real* cm, const Real* phi, int stride, Real* out) {
     static_assert(NF % 4 == 0, "whole vectors per mode");
@@ -206,8 +193,9 @@ __device__ __forceinline__ void point_fields_mm(const Real* cm, const Real* phi,
     }
 }
 
-// the same sums as point_fields<Real, NB, 5> over mode-major coefficients cm[j * NFP + v]
-// (rows 16-byte aligned): per mode one vector load of variables 0-3 and one load of variable 4
+// values at one point of 5 fields, out[v] = sum_j cm[j * NFP + v] phi[j * stride] summed in
+// increasing j, from mode-major coefficients (rows 16-byte aligned): per mode one vector load of
+// variables 0-3 and one load of variable 4
 template <typename Real, int NB, int NFP>
 __device__ __forceinline__ void point_fields5_mm(const Real* cm, const Real* phi, int stride, Real* out) {
 #pragma unroll
